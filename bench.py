@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark: one-ring neighbor CSR build throughput on GB300.
+
+One step = one full build of BOTH results (neighbor-node CSR and
+neighbor-element CSR) for one seeded synthetic mesh, through the C ABI, with
+the connectivity already resident in HBM.  Metric: Melem/s (mesh elements
+processed per second, whole job).  Default workload: the 2048 x 2048
+triangle grid (4,194,304 nodes, 8,380,418 triangles, node ids and element
+order permuted).
+
+Prints ONE JSON line (rank 0).  See the design doc for the roofline accounting.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank builds its own replica of the workload on its
+own GPU (weak scaling, no collective on the data path); the timed region is
+bracketed by barriers and the max over ranks is reported.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (meshgen call, description)
+    "tri2048": ("config_mesh(1)", "triangle grid 2048x2048 (4,194,304 nodes, 8,380,418 tris), seed 1, "
+                                  "random diagonals, node ids and element order permuted"),
+    "tri2048_holes": ("config_mesh(1, 'holes')", "triangle grid 2048x2048 with 5% of triangles deleted, seed 100"),
+    "tet161": ("config_mesh(2)", "Kuhn tet grid 161^3 (4,173,281 nodes, 24,576,000 tets), seed 2, permuted"),
+    "hex257": ("config_mesh(3)", "hex grid 257^3 (16,974,593 nodes, 16,777,216 hexes), seed 3, node ids permuted"),
+    "mixed257": ("config_mesh(3, 'mixed')", "hex grid 257^3 with 30% of cells split into 6 tets, seed 103"),
+    "tri64": ("config_mesh(0)", "triangle grid 64x64 (4,096 nodes, 7,938 tris), seed 0, permuted"),
+}
+WANT = {"both": 3, "nodes": 1, "elems": 2}
+KERNEL_OF_STAGE = {"hist": "k_hist", "offsets": "k_offsets", "part": "k_part", "bucket": "k_bucket"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="tri2048")
+    ap.add_argument("--want", choices=list(WANT), default="both")
+    ap.add_argument("--no-baseline", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_mesh(name):
+    from paper_1604_04689_gb300 import meshgen  # noqa: F401
+    return eval("meshgen." + WORKLOADS[name][0])
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                        rows.append(parts)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows)
+        reasons = set()
+        for r in rows:
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                 r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(rows[0][2]), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- baseline
+
+def oracle_baseline(seconds_hint=20.0):
+    """The CPU oracle, as it stands, on a bounded sample of the same kind of mesh."""
+    import oracle
+    from paper_1604_04689_gb300 import meshgen
+    n = 1024
+    mesh = meshgen.tri_grid(n, 1)
+    t0 = time.perf_counter()
+    r = oracle.neighbors(mesh, oracle.BOTH)
+    dt = time.perf_counter() - t0
+    assert r["status"] == 0
+    return {"value": mesh.n_elems / dt / 1e6, "unit": "Melem/s", "cores": 1, "kind": "oracle",
+            "sample": f"triangle grid {n}x{n} ({mesh.n_elems} tris, seed 1, permuted), both CSRs, "
+                      f"single-threaded std::set oracle, {dt:.1f} s"}
+
+
+def reference_arm(args):
+    """--impl reference: the CPU oracle timed on a bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_1604_04689_gb300 import meshgen
+    n = 256
+    mesh = meshgen.tri_grid(n, 1)
+    for _ in range(args.warmup):
+        oracle.neighbors(mesh, WANT[args.want])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = oracle.neighbors(mesh, WANT[args.want])
+        assert r["status"] == 0
+    dt = time.perf_counter() - t0
+    v = mesh.n_elems * args.steps / dt / 1e6
+    sample = (f"triangle grid {n}x{n} ({mesh.n_elems} tris, seed 1, permuted) per step, single-threaded "
+              f"std::set oracle on the host")
+    line = {"metric": "neighbor_csr_build_throughput", "value": v, "unit": "Melem/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "want": args.want, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "Melem/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "Melem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- ours
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1604_04689_gb300 import nn
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    want = WANT[args.want]
+    mesh = make_mesh(args.workload)
+    b = nn.Builder(dev)
+    dm = nn.DeviceMesh.from_host(mesh, device=dev)
+    ws_bytes, ncap, ecap = b.query(dm, want)
+    plan = nn.nn_plan_info(b.h, dm.struct(), want)
+    ws = b.workspace(ws_bytes)
+    out = b.alloc_outputs(dm, want)
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20), dtype=torch.uint8, device=dev)
+
+    def step():
+        st = b.launch(dm, want, out, ws=ws, ws_bytes=ws_bytes)
+        if st:
+            raise nn.NNError(st, "launch")
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+    assert int(b.status.item()) == 0, nn.STATUS[int(b.status.item())]
+
+    # ---- timed region: K builds, L2 flushed before each (outside the events)
+    sampler = ClockSampler(local)
+    if not args.no_clocks:
+        sampler.start()
+        time.sleep(0.3)
+    nn.nn_profile_enable(b.h, True)
+    stream = torch.cuda.current_stream(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    stage_ms, calls = nn.nn_profile_read(b.h)
+    nn.nn_profile_enable(b.h, False)
+    clocks = None if args.no_clocks else sampler.stop()
+    status = int(b.status.item())
+    assert status == 0, nn.STATUS[status]
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # ---- result sizes and algorithmic bytes
+    nnz = {}
+    for k, (rp, col) in out.items():
+        nnz[k] = int(rp[-1].item())
+    N, T, n_conn = mesh.n_nodes, mesh.n_elems, mesh.n_conn
+    rb, G, B = plan["record_bytes"], plan["emit_ctas"], plan["n_buckets"]
+    out_bytes = sum(8 * (N + 1) + 4 * v for v in nnz.values())
+    alg = {  # compulsory bytes each stage must move, per launch
+        "hist": 4 * n_conn + 4 * G * B,
+        "offsets": 3 * 4 * G * B + 4 * (B + 1),
+        "part": 4 * n_conn + 4 * G * B + rb * n_conn,
+        "bucket": rb * n_conn + 4 * (B + 1) + out_bytes,
+    }
+    pipeline_bytes = 4 * n_conn + out_bytes      # read connectivity once, write the CSRs once
+    peak, peak_src = measured_peaks()
+    dom = max(alg, key=lambda k: stage_ms.get(k, 0.0))
+    dom_ms = stage_ms[dom] / max(calls, 1)
+    achieved = alg[dom] / (dom_ms * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            with open(tpath) as f:
+                tr = json.load(f)
+            key = f"{args.workload}:{args.want}:{KERNEL_OF_STAGE[dom]}"
+            if key in tr and tr[key].get("source") == source_digest():
+                traffic = tr[key]["bytes_per_launch"]
+        except Exception:
+            traffic = None
+    ms_per_step = total_ms / args.steps
+    value = world * T * args.steps / (total_ms * 1e-3) / 1e6
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(torch, nn, b, mesh, dm, want, ws, ws_bytes, out, args.steps, dev, world)
+
+    baseline = None
+    if rank == 0 and world == 1 and not args.no_baseline:
+        baseline = oracle_baseline()
+
+    line = {
+        "metric": "neighbor_csr_build_throughput",
+        "value": value, "unit": "Melem/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload][1],
+                   "want": args.want, "n_nodes": N, "n_elems": T, "nnz": nnz,
+                   "l2": f"flushed before every timed step ({flush.numel() >> 20} MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU", "plan": plan},
+        "roofline": {"bound": "hbm", "kernel": KERNEL_OF_STAGE[dom], "achieved": achieved, "peak": peak,
+                     "peak_source": f"{peak_src} copy bandwidth", "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "alg_bytes_per_launch": alg[dom], "ms_per_launch": dom_ms},
+        "pipeline": {"alg_bytes_per_step": pipeline_bytes,
+                     "achieved_gbs": pipeline_bytes / (ms_per_step * 1e-3) / 1e9,
+                     "frac": pipeline_bytes / (ms_per_step * 1e-3) / 1e9 / peak,
+                     "stage_ms_per_step": {k: v / max(calls, 1) for k, v in stage_ms.items()},
+                     "wall_s": t_wall},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": baseline,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def end_to_end(torch, nn, b, mesh, dm, want, ws, ws_bytes, out, steps, dev, world):
+    """Same metric through the C ABI with host buffers: every step copies the
+    connectivity host->device from pinned memory, builds, and copies both CSRs
+    device->host into pinned memory (row pointers, then the used part of col)."""
+    h_conn = torch.from_numpy(mesh.conn).pin_memory()
+    d_conn = torch.empty_like(dm.conn)
+    dm2 = nn.DeviceMesh(dm.etype, dm.n_nodes, d_conn, dm.elem_ptr, dm.elem_type)
+    h_rp = {k: torch.empty(rp.numel(), dtype=torch.int64, pin_memory=True) for k, (rp, _) in out.items()}
+    h_col = {k: torch.empty(col.numel(), dtype=torch.int32, pin_memory=True) for k, (_, col) in out.items()}
+    stream = torch.cuda.current_stream(dev)
+    h2d = d2h = 0
+
+    def one():
+        nonlocal h2d, d2h
+        d_conn.copy_(h_conn, non_blocking=True)
+        st = b.launch(dm2, want, out, ws=ws, ws_bytes=ws_bytes)
+        if st:
+            raise nn.NNError(st, "launch")
+        for k, (rp, _) in out.items():
+            h_rp[k].copy_(rp, non_blocking=True)
+        stream.synchronize()
+        for k, (_, col) in out.items():
+            n = int(h_rp[k][-1])
+            h_col[k][:n].copy_(col[:n], non_blocking=True)
+            d2h += 8 * h_rp[k].numel() + 4 * n
+        stream.synchronize()
+        h2d += h_conn.numel() * 4
+
+    one()
+    h2d = d2h = 0
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    dt = time.perf_counter() - t0
+    if int(b.status.item()) != 0:
+        raise RuntimeError("device status after end-to-end leg: " + nn.STATUS[int(b.status.item())])
+    return {"value": world * mesh.n_elems * steps / dt / 1e6, "unit": "Melem/s",
+            "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
+            "ms_per_step": dt * 1e3 / steps}
+
+
+def source_digest():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1604_04689_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,146 @@
+/*
+ * nn.h -- one-ring neighbor nodes and neighbor elements of generic meshes,
+ * built on an NVIDIA GB300 (sm_103a).  C ABI of libnn.so.
+ *
+ * The operation (Mei et al., "A Parallel Solution to Finding Nodal Neighbors
+ * in Generic Meshes", Sec. 1 and Sec. 2.1):
+ *   - the neighbor NODES of node v are the nodes joined to v by an element
+ *     edge (Sec. 2.1.1; each edge makes its two nodes neighbors of each other);
+ *   - the neighbor ELEMENTS of v are the elements that contain v (Sec. 2.1.2).
+ * Both are returned as canonical CSR over all n_nodes nodes: row_ptr int64
+ * [n_nodes+1] with row_ptr[0] = 0, col int32, each row strictly ascending
+ * (a set: no repeats, no self entry).  Nodes that no element touches have
+ * empty rows.  An edge whose two ends are the same node is ignored.
+ *
+ * Element types and their local edge tables (local node indices):
+ *   NN_TRI  (3 nodes)  01 12 20
+ *   NN_QUAD (4 nodes)  01 12 23 30          (diagonals are not edges)
+ *   NN_TET  (4 nodes)  all six pairs
+ *   NN_HEX  (8 nodes, VTK order: 0-3 bottom face, 4-7 top face, i above i-4)
+ *                      01 12 23 30 45 56 67 74 04 15 26 37
+ *   NN_MIXED           per-element type in elem_type[], nodes of element e at
+ *                      conn[elem_ptr[e] .. elem_ptr[e+1])
+ * Element ids are positions in the element list (0-based); node ids are
+ * 0-based and must lie in [0, n_nodes).
+ *
+ * Memory and streams.  Every pointer in nn_mesh / nn_csr and the workspace
+ * are DEVICE pointers owned by the caller.  Compute calls only enqueue work
+ * on `stream` and return; nothing synchronises.  The library allocates no
+ * device memory on these paths (all scratch lives in the caller's workspace).
+ *
+ * Errors.  A call returns a host status for errors it can see without
+ * touching the device (bad arguments, workspace too small).  Errors found on
+ * the device are written to *d_status (device int32; the call first sets it
+ * to 0): node id out of range, inconsistent elem_ptr/elem_type, output
+ * capacity exceeded, spill workspace exhausted, or a bounded wait that timed
+ * out.  Kernels never trap; output contents are unspecified when *d_status
+ * is not NN_OK.  The number of entries written is row_ptr[n_nodes].
+ *
+ * Limits of this version: n_nodes, n_elems and n_conn each < 2^31; conn
+ * 16-byte aligned; the packed per-incidence record (see nn_query) must fit
+ * 128 bits, which holds for meshes up to roughly 2^27 nodes and elements.
+ */
+#ifndef NN_H
+#define NN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (the CUDA runtime's stream handle); 0 = legacy default stream. */
+typedef struct CUstream_st* nn_stream_t;
+
+typedef enum { NN_TRI = 0, NN_QUAD = 1, NN_TET = 2, NN_HEX = 3, NN_MIXED = 255 } nn_elem_type;
+
+typedef enum {
+    NN_OK = 0,
+    NN_ERR_ARG = 1,        /* null/misaligned pointer, bad type, size out of range  */
+    NN_ERR_WORKSPACE = 2,  /* ws_bytes below nn_query's minimum (host), or the spill
+                              part of the workspace ran out (device)                 */
+    NN_ERR_CAPACITY = 3,   /* an output col buffer is smaller than the result        */
+    NN_ERR_NODE_RANGE = 4, /* a node id outside [0, n_nodes) (device)                */
+    NN_ERR_ELEM_PTR = 5,   /* mixed mesh: unknown type or elem_ptr range of the wrong
+                              length / outside conn (device)                         */
+    NN_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up (device)            */
+    NN_ERR_BUDGET = 7,     /* serving layer: request larger than the memory budget   */
+    NN_ERR_CUDA = 8        /* a CUDA launch or driver call failed                    */
+} nn_status;
+
+/* want flags */
+#define NN_WANT_NODES 1
+#define NN_WANT_ELEMS 2
+#define NN_WANT_BOTH 3
+
+typedef struct {
+    int32_t type;              /* nn_elem_type                                        */
+    int64_t n_nodes;           /* rows of the result                                  */
+    int64_t n_elems;           /* elements                                            */
+    int64_t n_conn;            /* length of conn (n_elems * nodes-per-element unless
+                                  NN_MIXED)                                           */
+    const int32_t* conn;       /* device, int32 node ids, 16-byte aligned             */
+    const int64_t* elem_ptr;   /* device, [n_elems+1], NN_MIXED only (else NULL)      */
+    const uint8_t* elem_type;  /* device, [n_elems], NN_MIXED only (else NULL)        */
+} nn_mesh;
+
+typedef struct {
+    int64_t* row_ptr;          /* device, int64 [n_nodes+1]                           */
+    int32_t* col;              /* device, int32 [col_capacity]                        */
+    int64_t col_capacity;      /* entries available in col                            */
+} nn_csr;
+
+typedef struct nn_handle nn_handle;
+
+/* Create a handle bound to the current CUDA device (reads its SM count and
+ * shared-memory limits; holds launch tuning).  Host allocation only. */
+nn_status nn_create(nn_handle** h);
+void nn_destroy(nn_handle* h);
+
+/* Host-only sizing for a mesh (no device access).  want = NN_WANT_*.
+ * *ws_bytes: workspace that a compute call needs (the minimum plus a spill
+ * area sized for meshes of ordinary valence; meshes with a few nodes of very
+ * high valence may need more, reported as NN_ERR_WORKSPACE on the device).
+ * *node_col_cap / *elem_col_cap: upper bounds on the result sizes (the sum
+ * of local edge ends over all elements, and n_conn).  Any pointer may be NULL. */
+nn_status nn_query(nn_handle* h, const nn_mesh* mesh, int want, size_t* ws_bytes,
+                   int64_t* node_col_cap, int64_t* elem_col_cap);
+
+/* Parameters of the build plan for a mesh (host-only; for tooling and
+ * traffic accounting).  Fills up to n of: info[0] bucket shift (a bucket is
+ * 2^info[0] consecutive node ids), [1] number of buckets, [2] CTAs of the
+ * element walk, [3] bytes per incidence record, [4] minimum workspace bytes,
+ * [5] CTAs of the bucket pass. */
+nn_status nn_plan_info(nn_handle* h, const nn_mesh* mesh, int want, int64_t* info, int n);
+
+/* Neighbor nodes of every node (Sec. 2.1.1, Sec. 2.2.1) into *out. */
+nn_status nn_neighbor_nodes(nn_handle* h, const nn_mesh* mesh, nn_csr* out, void* ws,
+                            size_t ws_bytes, int32_t* d_status, nn_stream_t stream);
+
+/* Neighbor elements of every node (Sec. 2.1.2, Sec. 2.2.2) into *out. */
+nn_status nn_neighbor_elements(nn_handle* h, const nn_mesh* mesh, nn_csr* out, void* ws,
+                               size_t ws_bytes, int32_t* d_status, nn_stream_t stream);
+
+/* Both results from one pass over the connectivity (shares the element walk). */
+nn_status nn_neighbors_both(nn_handle* h, const nn_mesh* mesh, nn_csr* nodes, nn_csr* elems,
+                            void* ws, size_t ws_bytes, int32_t* d_status, nn_stream_t stream);
+
+/* Per-stage device timing (used by the benchmark).  While enabled, compute
+ * calls record CUDA events on their stream between their stages:
+ *   0 workspace/status init, 1 bucket histogram, 2 bucket offsets,
+ *   3 partition (record write), 4 bucket build (rows + CSR write).
+ * nn_profile_read waits for the recorded events and returns, per stage, the
+ * summed milliseconds over the calls since profiling was enabled, and the
+ * number of calls.  n_stages <= 5.  Enabling twice resets the sums. */
+nn_status nn_profile_enable(nn_handle* h, int enable);
+nn_status nn_profile_read(nn_handle* h, double* ms, int64_t* calls, int n_stages);
+
+/* Short English text for a status code (static storage). */
+const char* nn_status_str(nn_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NN_H */

@@ -1,15 +1,7 @@
 """One-ring neighbor nodes and elements of generic meshes on GB300 (sm_103a).
 
 The compute path is the CUDA library ``libnn.so`` (sources in ``csrc/``,
-C interface in ``include/nn.h``); ``nn`` is its thin ctypes binding and is
-loaded on first use, so ``meshgen`` stays importable on machines without a GPU.
+C interface in ``include/nn.h``); ``nn`` is its thin ctypes binding, which
+loads the library on first use, so ``meshgen`` stays importable on machines
+without a GPU.
 """
-
-__all__ = ["meshgen", "nn"]
-
-
-def __getattr__(name):
-    if name == "nn":
-        from . import nn as _nn
-        return _nn
-    raise AttributeError(name)

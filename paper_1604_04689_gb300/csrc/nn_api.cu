@@ -1,0 +1,383 @@
+// Host side of libnn: argument checks, the build plan (bucket width, record
+// format, workspace layout) and the launch sequence.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "nn_internal.h"
+
+namespace nn {
+cudaError_t set_emit_smem_all(size_t bytes);
+cudaError_t set_bucket_smem_all(size_t bytes);
+cudaError_t bucket_occupancy(int* blocks, int threads, size_t smem);
+int bucket_threads();
+}  // namespace nn
+
+struct nn_handle {
+    int device = 0;
+    int sms = 0;
+    size_t smem_optin = 0;     // max dynamic shared memory per block
+    size_t bucket_smem = 0;    // dynamic shared memory of the bucket kernel
+    int bucket_blocks_per_sm = 1;
+    int sb_override = -1;      // fixed bucket width (tests / tuning), -1 = automatic
+    // per-stage timing (nn_profile_*)
+    bool prof = false;
+    bool pending = false;
+    cudaEvent_t ev[6] = {};
+    double acc[5] = {};
+    int64_t calls = 0;
+};
+
+namespace {
+
+using namespace nn;
+
+constexpr size_t ALIGN = 256;
+constexpr int SB_MIN = 4, SB_MAX = 11;
+constexpr size_t BUCKET_FIXED_PER_NODE = 28;  // bytes of per-node arrays in the bucket kernel
+constexpr size_t BUCKET_FIXED = 34 * 8 + 8 * 8;
+
+size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+int bits_for(uint64_t x) {  // bits needed to hold values 0..x (>= 1)
+    int b = 1;
+    while (b < 64 && (x >> b)) ++b;
+    return b;
+}
+int npe_host(int t) { return t == NN_TRI ? 3 : (t == NN_HEX ? 8 : 4); }
+
+struct Plan {
+    int type = 0, want = 0, k = 0;
+    int64_t N = 0, T = 0, n_conn = 0;
+    RecFmt fmt{};
+    int64_t B = 0;
+    int G = 1;
+    size_t emit_smem = 0;
+    size_t off_hist = 0, off_bstart = 0, off_rec = 0, off_lb_off = 0, off_lb_n = 0, off_lb_e = 0,
+           off_ctrl = 0, off_spill = 0, zero_begin = 0, zero_end = 0;
+    size_t ws_min = 0, ws_rec = 0;
+    int bucket_grid = 0;
+    uint32_t area_words = 0;
+};
+
+nn_status check_mesh(const nn_mesh* m) {
+    if (!m) return NN_ERR_ARG;
+    const int t = m->type;
+    if (!(t == NN_TRI || t == NN_QUAD || t == NN_TET || t == NN_HEX || t == NN_MIXED)) return NN_ERR_ARG;
+    if (m->n_nodes < 0 || m->n_elems < 0 || m->n_conn < 0) return NN_ERR_ARG;
+    if (m->n_nodes >= (1ll << 31) || m->n_elems >= (1ll << 31) || m->n_conn >= (1ll << 31)) return NN_ERR_ARG;
+    if (t != NN_MIXED && m->n_conn != m->n_elems * npe_host(t)) return NN_ERR_ARG;
+    if (m->n_conn > 0 && !m->conn) return NN_ERR_ARG;
+    if (t != NN_MIXED && (reinterpret_cast<uintptr_t>(m->conn) & 15)) return NN_ERR_ARG;
+    if (t == NN_MIXED && m->n_elems > 0 && (!m->elem_ptr || !m->elem_type)) return NN_ERR_ARG;
+    if (t == NN_MIXED && (reinterpret_cast<uintptr_t>(m->elem_ptr) & 7)) return NN_ERR_ARG;
+    return NN_OK;
+}
+
+nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
+    nn_status st = check_mesh(m);
+    if (st != NN_OK) return st;
+    if (want < 1 || want > 3) return NN_ERR_ARG;
+    Plan p;
+    p.type = m->type;
+    p.want = want;
+    p.N = m->n_nodes;
+    p.T = m->n_elems;
+    p.n_conn = m->n_conn;
+    p.k = (m->type == NN_TRI || m->type == NN_QUAD) ? 2 : 3;
+
+    // bucket width: as many nodes as fit the bucket kernel's shared memory
+    // with room to spare for nodes of higher than average valence
+    const double inc = p.N > 0 ? (double)p.n_conn / (double)p.N : 0.0;
+    const double E = (want & NN_WANT_ELEMS) ? inc : 0.0;
+    const double C = (want & NN_WANT_NODES) ? p.k * inc : 0.0;
+    double Tt = 0.0;
+    if (C > 0) {
+        Tt = 2;
+        while (Tt <= std::ceil(C)) Tt *= 2;
+    }
+    const double per_node = 4.0 * (E + Tt + 0.5 * C);  // list + table + staged row, bytes
+    int sb = SB_MIN;
+    for (int s = SB_MAX; s >= SB_MIN; --s) {
+        const double area = (double)h->bucket_smem - (double)BUCKET_FIXED_PER_NODE * (1 << s) - BUCKET_FIXED;
+        if (area > 0 && (double)(1 << s) * per_node <= 0.6 * area) {
+            sb = s;
+            break;
+        }
+    }
+    if (h->sb_override >= SB_MIN && h->sb_override <= SB_MAX) sb = h->sb_override;
+    // the bucket kernel's per-node arrays must leave room for its list/table area
+    auto fixed_of = [](int s) { return BUCKET_FIXED_PER_NODE * ((size_t)1 << s) + BUCKET_FIXED; };
+    const size_t min_area = 4096 * 4;
+    while (sb > SB_MIN && fixed_of(sb) + min_area > h->bucket_smem) --sb;
+    const int64_t B_max = (int64_t)((h->smem_optin - 1024) / 4);
+    auto nbk = [&](int s) { return (p.N + (1ll << s) - 1) >> s; };
+    while (nbk(sb) > B_max && sb < SB_MAX) ++sb;
+    if (nbk(sb) > B_max || fixed_of(sb) + min_area > h->bucket_smem) return NN_ERR_ARG;
+    p.B = nbk(sb);
+
+    RecFmt& f = p.fmt;
+    f.sb = sb;
+    f.want = want;
+    f.k = p.k;
+    f.eb = bits_for(p.T > 0 ? (uint64_t)(p.T - 1) : 0);
+    f.nb = bits_for((uint64_t)p.N);
+    f.off_nf = sb;
+    f.off_e = sb + 1;
+    f.off_n = (want & NN_WANT_ELEMS) ? sb + 1 + f.eb : sb;
+    int total = (want & NN_WANT_NODES) ? f.off_n + p.k * f.nb : sb + 1 + f.eb;
+    if (total > 128) return NN_ERR_ARG;
+    f.rb = total <= 64 ? 8 : 16;
+
+    // element-walk CTAs: one or two per SM, each a fixed slice of elements
+    const int unit = p.type == NN_TRI ? 4 : 1;
+    const int64_t n_units = (p.T + unit - 1) / unit;
+    p.emit_smem = std::max<size_t>(16, (size_t)p.B * 4);
+    const int cps = p.emit_smem + 2048 <= 113 * 1024 ? 2 : 1;
+    p.G = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sms * cps, (n_units + 2047) / 2048));
+
+    // workspace layout
+    size_t o = 0;
+    p.off_hist = o; o = align_up(o + (size_t)p.G * p.B * 4);
+    p.off_bstart = o; o = align_up(o + ((size_t)p.B + 1) * 4);
+    p.off_rec = o; o = align_up(o + (size_t)p.n_conn * f.rb);
+    p.zero_begin = o;
+    p.off_lb_off = o; o = align_up(o + (size_t)((p.B + OFFSETS_THREADS - 1) / OFFSETS_THREADS) * 8 + 8);
+    p.off_lb_n = o; o = align_up(o + ((want & NN_WANT_NODES) ? (size_t)p.B * 8 : 0));
+    p.off_lb_e = o; o = align_up(o + ((want & NN_WANT_ELEMS) ? (size_t)p.B * 8 : 0));
+    p.off_ctrl = o; o = align_up(o + 64);
+    p.zero_end = o;
+    p.off_spill = o;
+    p.ws_min = o;
+    const size_t spill = (want & NN_WANT_NODES) ? ((size_t)16 << 20) + (size_t)p.n_conn * 8 : 0;
+    p.ws_rec = o + spill;
+
+    const size_t fixed = BUCKET_FIXED_PER_NODE * ((size_t)1 << sb) + BUCKET_FIXED;
+    p.area_words = (uint32_t)((h->bucket_smem - fixed) / 4);
+    p.bucket_grid = (int)std::min<int64_t>(p.B, (int64_t)h->sms * h->bucket_blocks_per_sm);
+    *P = p;
+    return NN_OK;
+}
+
+void prof_flush(nn_handle* h) {
+    if (!h->pending) return;
+    h->pending = false;
+    if (cudaEventSynchronize(h->ev[5]) != cudaSuccess) return;
+    for (int i = 0; i < 5; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]) == cudaSuccess) h->acc[i] += ms;
+    }
+    h->calls += 1;
+}
+
+void prof_mark(nn_handle* h, int i, cudaStream_t s) {
+    if (h->prof) cudaEventRecord(h->ev[i], s);
+}
+
+nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* elems, void* ws,
+              size_t ws_bytes, int32_t* d_status, cudaStream_t s) {
+    if (!h || !d_status) return NN_ERR_ARG;
+    Plan p;
+    nn_status st = make_plan(h, m, want, &p);
+    if (st != NN_OK) return st;
+    if ((want & NN_WANT_NODES) && (!nodes || !nodes->row_ptr || nodes->col_capacity < 0 ||
+                                   (nodes->col_capacity > 0 && !nodes->col)))
+        return NN_ERR_ARG;
+    if ((want & NN_WANT_ELEMS) && (!elems || !elems->row_ptr || elems->col_capacity < 0 ||
+                                   (elems->col_capacity > 0 && !elems->col)))
+        return NN_ERR_ARG;
+    if (ws_bytes < p.ws_min || (!ws && p.ws_min > 0)) return NN_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(ws) & (ALIGN - 1)) return NN_ERR_ARG;
+
+    uint8_t* w = static_cast<uint8_t*>(ws);
+    if (h->prof) prof_flush(h);
+    prof_mark(h, 0, s);
+    if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return NN_ERR_CUDA;
+    if (p.N == 0) {
+        if ((want & NN_WANT_NODES) && cudaMemsetAsync(nodes->row_ptr, 0, 8, s) != cudaSuccess) return NN_ERR_CUDA;
+        if ((want & NN_WANT_ELEMS) && cudaMemsetAsync(elems->row_ptr, 0, 8, s) != cudaSuccess) return NN_ERR_CUDA;
+        return NN_OK;
+    }
+    if (cudaMemsetAsync(w + p.zero_begin, 0, p.zero_end - p.zero_begin, s) != cudaSuccess) return NN_ERR_CUDA;
+
+    uint32_t* ctrl = reinterpret_cast<uint32_t*>(w + p.off_ctrl);
+    EmitParams ep{};
+    ep.type = p.type;
+    ep.n_nodes = p.N;
+    ep.n_elems = p.T;
+    ep.n_conn = p.n_conn;
+    ep.conn = m->conn;
+    ep.elem_ptr = m->elem_ptr;
+    ep.elem_type = m->elem_type;
+    ep.fmt = p.fmt;
+    ep.n_buckets = p.B;
+    ep.n_cta = p.G;
+    ep.hist = reinterpret_cast<uint32_t*>(w + p.off_hist);
+    ep.rec = w + p.off_rec;
+    ep.rec_cap = (uint64_t)p.n_conn;
+    ep.status = d_status;
+
+    OffsetsParams op{};
+    op.hist = ep.hist;
+    op.n_cta = p.G;
+    op.n_buckets = p.B;
+    op.bstart = reinterpret_cast<uint32_t*>(w + p.off_bstart);
+    op.lb_state = reinterpret_cast<uint64_t*>(w + p.off_lb_off);
+    op.ticket = ctrl + 0;
+    op.rec_cap = (uint64_t)p.n_conn;
+    op.status = d_status;
+
+    BucketParams bp{};
+    bp.fmt = p.fmt;
+    bp.n_nodes = p.N;
+    bp.n_buckets = p.B;
+    bp.rec = ep.rec;
+    bp.bstart = op.bstart;
+    bp.lb_n = reinterpret_cast<uint64_t*>(w + p.off_lb_n);
+    bp.lb_e = reinterpret_cast<uint64_t*>(w + p.off_lb_e);
+    bp.ticket = ctrl + 1;
+    bp.spill_cursor = reinterpret_cast<unsigned long long*>(ctrl + 2);
+    bp.spill = reinterpret_cast<uint32_t*>(w + p.off_spill);
+    bp.spill_words = ws_bytes > p.off_spill ? (ws_bytes - p.off_spill) / 4 : 0;
+    if (want & NN_WANT_NODES) {
+        bp.rp_n = nodes->row_ptr;
+        bp.col_n = nodes->col;
+        bp.cap_n = nodes->col_capacity;
+    }
+    if (want & NN_WANT_ELEMS) {
+        bp.rp_e = elems->row_ptr;
+        bp.col_e = elems->col;
+        bp.cap_e = elems->col_capacity;
+    }
+    bp.status = d_status;
+    bp.area_words = p.area_words;
+
+    prof_mark(h, 1, s);
+    if (launch_hist(ep, p.emit_smem, s) != cudaSuccess) return NN_ERR_CUDA;
+    prof_mark(h, 2, s);
+    if (launch_offsets(op, s) != cudaSuccess) return NN_ERR_CUDA;
+    prof_mark(h, 3, s);
+    if (launch_part(ep, p.emit_smem, s) != cudaSuccess) return NN_ERR_CUDA;
+    prof_mark(h, 4, s);
+    if (launch_bucket(bp, p.bucket_grid, bucket_threads(), h->bucket_smem, s) != cudaSuccess)
+        return NN_ERR_CUDA;
+    prof_mark(h, 5, s);
+    if (h->prof) h->pending = true;
+    return NN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nn_status nn_create(nn_handle** out) {
+    if (!out) return NN_ERR_ARG;
+    nn_handle* h = new (std::nothrow) nn_handle();
+    if (!h) return NN_ERR_ARG;
+    int optin = 0;
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess) {
+        delete h;
+        return NN_ERR_CUDA;
+    }
+    h->smem_optin = (size_t)optin;
+    h->bucket_smem = h->smem_optin;
+    if (const char* e = std::getenv("NN_SB")) h->sb_override = std::atoi(e);
+    if (const char* e = std::getenv("NN_BUCKET_SMEM_KB")) {
+        size_t kb = (size_t)std::atol(e);
+        if (kb >= 32 && kb * 1024 <= h->smem_optin) h->bucket_smem = kb * 1024;
+    }
+    if (set_emit_smem_all(h->smem_optin) != cudaSuccess || set_bucket_smem_all(h->smem_optin) != cudaSuccess) {
+        delete h;
+        return NN_ERR_CUDA;
+    }
+    int blocks = 0;
+    if (bucket_occupancy(&blocks, bucket_threads(), h->bucket_smem) != cudaSuccess || blocks < 1) blocks = 1;
+    h->bucket_blocks_per_sm = blocks;
+    *out = h;
+    return NN_OK;
+}
+
+void nn_destroy(nn_handle* h) {
+    if (!h) return;
+    for (cudaEvent_t e : h->ev)
+        if (e) cudaEventDestroy(e);
+    delete h;
+}
+
+nn_status nn_profile_enable(nn_handle* h, int enable) {
+    if (!h) return NN_ERR_ARG;
+    if (enable && !h->ev[0])
+        for (cudaEvent_t& e : h->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return NN_ERR_CUDA;
+    h->pending = false;
+    h->prof = enable != 0;
+    for (double& a : h->acc) a = 0.0;
+    h->calls = 0;
+    return NN_OK;
+}
+
+nn_status nn_profile_read(nn_handle* h, double* ms, int64_t* calls, int n_stages) {
+    if (!h || n_stages < 0 || n_stages > 5) return NN_ERR_ARG;
+    prof_flush(h);
+    for (int i = 0; i < n_stages; ++i) ms[i] = h->acc[i];
+    if (calls) *calls = h->calls;
+    return NN_OK;
+}
+
+nn_status nn_query(nn_handle* h, const nn_mesh* mesh, int want, size_t* ws_bytes, int64_t* node_col_cap,
+                   int64_t* elem_col_cap) {
+    if (!h) return NN_ERR_ARG;
+    Plan p;
+    nn_status st = make_plan(h, mesh, want, &p);
+    if (st != NN_OK) return st;
+    if (ws_bytes) *ws_bytes = p.ws_rec;
+    // bound on node entries: every incidence has at most k edge ends (2 tri/quad, 3 tet/hex)
+    if (node_col_cap) *node_col_cap = (int64_t)p.k * p.n_conn;
+    if (elem_col_cap) *elem_col_cap = p.n_conn;
+    return NN_OK;
+}
+
+nn_status nn_plan_info(nn_handle* h, const nn_mesh* mesh, int want, int64_t* info, int n) {
+    if (!h || (!info && n > 0) || n < 0) return NN_ERR_ARG;
+    Plan p;
+    nn_status st = make_plan(h, mesh, want, &p);
+    if (st != NN_OK) return st;
+    const int64_t v[6] = {p.fmt.sb, p.B, p.G, p.fmt.rb, (int64_t)p.ws_min, p.bucket_grid};
+    for (int i = 0; i < n && i < 6; ++i) info[i] = v[i];
+    return NN_OK;
+}
+
+nn_status nn_neighbor_nodes(nn_handle* h, const nn_mesh* mesh, nn_csr* out, void* ws, size_t ws_bytes,
+                            int32_t* d_status, nn_stream_t stream) {
+    return run(h, mesh, NN_WANT_NODES, out, nullptr, ws, ws_bytes, d_status, reinterpret_cast<cudaStream_t>(stream));
+}
+
+nn_status nn_neighbor_elements(nn_handle* h, const nn_mesh* mesh, nn_csr* out, void* ws, size_t ws_bytes,
+                               int32_t* d_status, nn_stream_t stream) {
+    return run(h, mesh, NN_WANT_ELEMS, nullptr, out, ws, ws_bytes, d_status, reinterpret_cast<cudaStream_t>(stream));
+}
+
+nn_status nn_neighbors_both(nn_handle* h, const nn_mesh* mesh, nn_csr* nodes, nn_csr* elems, void* ws,
+                            size_t ws_bytes, int32_t* d_status, nn_stream_t stream) {
+    return run(h, mesh, NN_WANT_BOTH, nodes, elems, ws, ws_bytes, d_status, reinterpret_cast<cudaStream_t>(stream));
+}
+
+const char* nn_status_str(nn_status s) {
+    switch (s) {
+        case NN_OK: return "ok";
+        case NN_ERR_ARG: return "invalid argument";
+        case NN_ERR_WORKSPACE: return "workspace too small";
+        case NN_ERR_CAPACITY: return "output capacity too small";
+        case NN_ERR_NODE_RANGE: return "node id out of range";
+        case NN_ERR_ELEM_PTR: return "element offsets inconsistent with element types";
+        case NN_ERR_TIMEOUT: return "device wait timed out";
+        case NN_ERR_BUDGET: return "request exceeds memory budget";
+        case NN_ERR_CUDA: return "CUDA error";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,270 @@
+// Bucket pass: builds the rows of one node range per CTA from its records.
+//
+// For the 2^sb nodes of a bucket the CTA counts, per node, the element
+// entries and the neighbour candidates of its records; lays out one element
+// list and one open-addressing hash table per node in shared memory (table
+// size = next power of two above the candidate count, so it never fills);
+// inserts the candidates (a repeated neighbour -- an edge shared by several
+// elements -- hits its own slot and is dropped); sorts each row; and writes
+// row_ptr and col of both CSRs at offsets found by a lookback scan over the
+// buckets, which are processed in node order.  A bucket whose lists and
+// tables do not fit shared memory keeps its tables in a global spill area
+// and its element lists directly in the output.
+//
+// Rows are sets in ascending order: the paper's pipeline (Sec. 2.2.1) sorts
+// pairs by key only and counts pairs per key, which lists an edge shared by
+// two elements twice; one-ring neighbours are a set (Sec. 1), so repeated
+// neighbours are dropped and each row is sorted.
+#include "nn_device.cuh"
+
+namespace nn {
+
+namespace {
+
+constexpr int BUCKET_THREADS = 512;
+constexpr int LONG_ROW = 48;  // rows longer than this are sorted by the whole block
+
+template <int RB>
+__device__ __forceinline__ Rec load_rec(const uint8_t* base, uint32_t r) {
+    Rec x;
+    if constexpr (RB == 8) {
+        x.lo = __ldg(reinterpret_cast<const unsigned long long*>(base) + r);
+        x.hi = 0;
+    } else {
+        ulonglong2 w = __ldg(reinterpret_cast<const ulonglong2*>(base) + r);
+        x.lo = w.x;
+        x.hi = w.y;
+    }
+    return x;
+}
+
+// Insert x into the open-addressing table tab[0..mask]; true if x was new.
+// The table has more slots than distinct values ever inserted; the probe
+// count is still bounded and an overrun reports NN_ERR_WORKSPACE.
+__device__ __forceinline__ bool tab_insert(uint32_t* tab, uint32_t mask, int shift, uint32_t x,
+                                           int32_t* status) {
+    uint32_t h = (x * 0x9E3779B1u) >> shift;
+    for (uint32_t probes = 0; probes <= mask; ++probes) {
+        uint32_t cur = *reinterpret_cast<volatile uint32_t*>(&tab[h]);
+        if (cur == x) return false;
+        if (cur == EMPTY) {
+            uint32_t old = atomicCAS(&tab[h], EMPTY, x);
+            if (old == EMPTY) return true;
+            if (old == x) return false;
+        }
+        h = (h + 1) & mask;
+    }
+    set_status(status, NN_ERR_WORKSPACE);
+    return false;
+}
+
+__device__ __forceinline__ uint32_t table_size(uint32_t c) {
+    if (c == 0) return 0;
+    uint32_t t = 2;
+    while (t <= c && t < 0x80000000u) t <<= 1;  // smallest power of two > c
+    return t;
+}
+
+template <int RB, int K>
+__global__ void __launch_bounds__(BUCKET_THREADS) k_bucket(BucketParams p) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const RecFmt f = p.fmt;
+    const int NB = 1 << f.sb;
+    const uint32_t vmask = (uint32_t)NB - 1;
+    uint64_t* cnt = reinterpret_cast<uint64_t*>(smem);  // [NB] counts / scan scratch
+    uint32_t* eoff = reinterpret_cast<uint32_t*>(cnt + NB);
+    uint32_t* toff = eoff + NB;
+    uint32_t* tsz = toff + NB;
+    uint32_t* ucnt = tsz + NB;
+    uint32_t* aux = ucnt + NB;                            // element cursor, then row offsets
+    uint64_t* sh_scan = reinterpret_cast<uint64_t*>(aux + NB);  // 34 words
+    uint64_t* misc = sh_scan + 34;                              // 8 words
+    uint32_t* area = reinterpret_cast<uint32_t*>(misc + 8);
+    const bool want_n = f.want & NN_WANT_NODES, want_e = f.want & NN_WANT_ELEMS;
+    const int tid = threadIdx.x, BS = blockDim.x;
+
+    for (;;) {
+        if (tid == 0) misc[0] = atomicAdd(p.ticket, 1u);
+        __syncthreads();
+        const int64_t b = (int64_t)misc[0];
+        __syncthreads();
+        if (b >= p.n_buckets) break;
+        const int64_t v0 = b << f.sb;
+        const int nb = (int)(p.n_nodes - v0 < (int64_t)NB ? p.n_nodes - v0 : (int64_t)NB);
+        const uint32_t r0 = p.bstart[b], r1 = p.bstart[b + 1];
+
+        // counts per node: element entries (high word) and candidates (low word)
+        for (int l = tid; l < NB; l += BS) cnt[l] = 0;
+        __syncthreads();
+        for (uint32_t r = r0 + tid; r < r1; r += BS) {
+            Rec x = load_rec<RB>(p.rec, r);
+            const uint32_t vloc = (uint32_t)x.lo & vmask;
+            uint64_t inc = 0;
+            if (want_e && !rec_get(x, f.off_nf, 1)) inc += 1ull << 32;
+            if (want_n) {
+#pragma unroll
+                for (int s = 0; s < K; ++s) inc += rec_get(x, f.off_n + s * f.nb, f.nb) != 0;
+            }
+            if (inc) atomicAdd(reinterpret_cast<unsigned long long*>(&cnt[vloc]), (unsigned long long)inc);
+        }
+        __syncthreads();
+        // element offsets
+        for (int l = tid; l < NB; l += BS) {
+            const uint64_t c = cnt[l];
+            tsz[l] = table_size((uint32_t)c);
+            ucnt[l] = 0;
+            aux[l] = 0;
+            cnt[l] = c >> 32;
+        }
+        __syncthreads();
+        const uint64_t Eb = smem_array_excl_scan(cnt, NB, sh_scan);
+        for (int l = tid; l < NB; l += BS) {
+            eoff[l] = (uint32_t)cnt[l];
+            cnt[l] = tsz[l];
+        }
+        __syncthreads();
+        const uint64_t Tb = smem_array_excl_scan(cnt, NB, sh_scan);
+        for (int l = tid; l < NB; l += BS) toff[l] = (uint32_t)cnt[l];
+        if (tid == 0) {
+            misc[1] = want_e ? lookback(p.lb_e, b, Eb, p.status) : 0;
+            const bool fast = Eb + Tb <= p.area_words;
+            uint64_t spill_off = 0;
+            bool tab_ok = true;
+            if (!fast && want_n && Tb > 0) {
+                spill_off = atomicAdd(p.spill_cursor, (unsigned long long)Tb);
+                if (spill_off + Tb > p.spill_words || Tb >= 0xFFFFFFFFull) {
+                    tab_ok = false;
+                    set_status(p.status, NN_ERR_WORKSPACE);
+                }
+            }
+            misc[2] = spill_off;
+            misc[4] = (fast ? 1 : 0) | (tab_ok ? 2 : 0);
+            if (want_e && misc[1] + Eb > (uint64_t)p.cap_e) set_status(p.status, NN_ERR_CAPACITY);
+        }
+        __syncthreads();
+        const uint64_t Ge = misc[1];
+        const bool fast = misc[4] & 1, tab_ok = (misc[4] & 2) && want_n;
+        const bool e_ok = want_e && Ge + Eb <= (uint64_t)p.cap_e;
+        uint32_t* elist = fast ? area : reinterpret_cast<uint32_t*>(p.col_e) + Ge;
+        const bool e_write = want_e && (fast || e_ok);
+        uint32_t* tab = fast ? area + Eb : p.spill + misc[2];
+        if (tab_ok)
+            for (uint64_t i = tid; i < Tb; i += BS) tab[i] = EMPTY;
+        __syncthreads();
+
+        // second pass: element lists and neighbour tables
+        for (uint32_t r = r0 + tid; r < r1; r += BS) {
+            Rec x = load_rec<RB>(p.rec, r);
+            const uint32_t vloc = (uint32_t)x.lo & vmask;
+            if (e_write && !rec_get(x, f.off_nf, 1)) {
+                const uint32_t q = atomicAdd(&aux[vloc], 1u);
+                elist[eoff[vloc] + q] = rec_get(x, f.off_e, f.eb);
+            }
+            if (tab_ok) {
+                const uint32_t T = tsz[vloc];
+                uint32_t* t = tab + toff[vloc];
+                const int shift = __clz(T) + 1;
+#pragma unroll
+                for (int s = 0; s < K; ++s) {
+                    const uint32_t y = rec_get(x, f.off_n + s * f.nb, f.nb);
+                    if (y && tab_insert(t, T - 1, shift, y - 1, p.status)) atomicAdd(&ucnt[vloc], 1u);
+                }
+            }
+        }
+        __syncthreads();
+        for (int l = tid; l < NB; l += BS) cnt[l] = ucnt[l];
+        __syncthreads();
+        const uint64_t Ub = smem_array_excl_scan(cnt, NB, sh_scan);
+        for (int l = tid; l < NB; l += BS) aux[l] = (uint32_t)cnt[l];
+        if (tid == 0) {
+            misc[3] = want_n ? lookback(p.lb_n, b, Ub, p.status) : 0;
+            if (want_n && misc[3] + Ub > (uint64_t)p.cap_n) set_status(p.status, NN_ERR_CAPACITY);
+        }
+        __syncthreads();
+        const uint64_t Gn = misc[3];
+        const bool n_ok = tab_ok && Gn + Ub <= (uint64_t)p.cap_n;
+
+        // row pointers
+        for (int l = tid; l < nb; l += BS) {
+            if (want_n) p.rp_n[v0 + l] = (int64_t)(Gn + aux[l]);
+            if (want_e) p.rp_e[v0 + l] = (int64_t)(Ge + eoff[l]);
+        }
+        if (b == p.n_buckets - 1 && tid == 0) {
+            if (want_n) p.rp_n[p.n_nodes] = (int64_t)(Gn + Ub);
+            if (want_e) p.rp_e[p.n_nodes] = (int64_t)(Ge + Eb);
+        }
+
+        // rows: gather each node's distinct neighbours from its table, sort
+        uint32_t* stage = (fast && Eb + Tb + Ub <= p.area_words) ? area + Eb + Tb : nullptr;
+        uint32_t* dst_n = stage ? stage : reinterpret_cast<uint32_t*>(p.col_n) + Gn;
+        if (n_ok) {
+            for (int l = tid; l < NB; l += BS) {
+                const uint32_t U = ucnt[l];
+                if (U == 0) continue;
+                uint32_t* d = dst_n + aux[l];
+                const uint32_t* t = tab + toff[l];
+                uint32_t j = 0;
+                for (uint32_t s = 0; s < tsz[l]; ++s) {
+                    const uint32_t y = t[s];
+                    if (y != EMPTY) d[j++] = y;
+                }
+                if (U <= LONG_ROW) insertion_sort(d, (int)U);
+            }
+        }
+        if (e_write) {
+            for (int l = tid; l < NB; l += BS) {
+                const uint32_t E = (l + 1 < NB ? eoff[l + 1] : (uint32_t)Eb) - eoff[l];
+                if (E > 1 && E <= LONG_ROW) insertion_sort(elist + eoff[l], (int)E);
+            }
+        }
+        __syncthreads();
+        for (int l = 0; l < NB; ++l) {  // uniform loop: long rows, whole block
+            if (n_ok && ucnt[l] > LONG_ROW) block_bitonic_sort(dst_n + aux[l], ucnt[l]);
+            if (e_write) {
+                const uint32_t E = (l + 1 < NB ? eoff[l + 1] : (uint32_t)Eb) - eoff[l];
+                if (E > LONG_ROW) block_bitonic_sort(elist + eoff[l], E);
+            }
+        }
+        __syncthreads();
+        if (stage && n_ok)
+            for (uint64_t i = tid; i < Ub; i += BS) p.col_n[Gn + i] = (int32_t)stage[i];
+        if (fast && e_ok)
+            for (uint64_t i = tid; i < Eb; i += BS) p.col_e[Ge + i] = (int32_t)elist[i];
+        __syncthreads();
+    }
+}
+
+template <int RB, int K>
+cudaError_t set_attr(size_t bytes) {
+    return cudaFuncSetAttribute(k_bucket<RB, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+int bucket_threads() { return BUCKET_THREADS; }
+
+cudaError_t launch_bucket(const BucketParams& p, int grid, int threads, size_t smem, cudaStream_t s) {
+    if (grid <= 0) return cudaSuccess;
+    if (p.fmt.rb == 8) {
+        if (p.fmt.k == 2) k_bucket<8, 2><<<grid, threads, smem, s>>>(p);
+        else k_bucket<8, 3><<<grid, threads, smem, s>>>(p);
+    } else {
+        if (p.fmt.k == 2) k_bucket<16, 2><<<grid, threads, smem, s>>>(p);
+        else k_bucket<16, 3><<<grid, threads, smem, s>>>(p);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t set_bucket_smem_all(size_t bytes) {
+    cudaError_t e = set_attr<8, 2>(bytes);
+    if (e == cudaSuccess) e = set_attr<8, 3>(bytes);
+    if (e == cudaSuccess) e = set_attr<16, 2>(bytes);
+    if (e == cudaSuccess) e = set_attr<16, 3>(bytes);
+    return e;
+}
+
+cudaError_t bucket_occupancy(int* blocks, int threads, size_t smem) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_bucket<16, 3>, threads, smem);
+}
+
+}  // namespace nn

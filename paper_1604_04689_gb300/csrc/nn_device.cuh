@@ -1,0 +1,224 @@
+// Device helpers shared by the libnn kernels: status reporting, bounded
+// decoupled lookback, block scans, record packing, element edge tables and
+// row sorting.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "nn_internal.h"
+
+namespace nn {
+
+constexpr uint32_t EMPTY = 0xFFFFFFFFu;
+// A bounded wait gives up after this long without progress (ns).
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
+
+__device__ __forceinline__ void set_status(int32_t* st, int32_t code) { atomicCAS(st, 0, code); }
+
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---------------------------------------------------------------- lookback
+// Single-pass scan across tiles taken in ticket order.  Word layout: bits
+// 62-63 flag (0 not ready, 1 tile aggregate, 2 inclusive prefix), bits 0-61
+// the value.  Every predecessor of a tile holds an earlier ticket, so it is
+// running or done; the wait is still bounded and reports NN_ERR_TIMEOUT.
+constexpr uint64_t LB_AGG = 1ull << 62;
+constexpr uint64_t LB_INC = 2ull << 62;
+constexpr uint64_t LB_VAL = (1ull << 62) - 1;
+
+// Called by ONE thread; returns the exclusive prefix of tile t.
+__device__ inline uint64_t lookback(uint64_t* state, uint64_t t, uint64_t agg, int32_t* status) {
+    if (t == 0) {
+        st_release(&state[0], LB_INC | agg);
+        return 0;
+    }
+    st_release(&state[t], LB_AGG | agg);
+    uint64_t excl = 0;
+    int64_t p = (int64_t)t - 1;
+    uint64_t t0 = 0;
+    while (p >= 0) {
+        uint64_t s = ld_acquire(&state[p]);
+        uint64_t flag = s >> 62;
+        if (flag == 0) {
+            uint64_t now = global_ns();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > WAIT_LIMIT_NS) {
+                set_status(status, NN_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(64);
+            continue;
+        }
+        t0 = 0;
+        excl += s & LB_VAL;
+        if (flag == 2) break;
+        --p;
+    }
+    st_release(&state[t], LB_INC | ((excl + agg) & LB_VAL));
+    return excl;
+}
+
+// ------------------------------------------------------------ block scans
+// Exclusive scan of one 64-bit value per thread; *total gets the block sum.
+// `sh` needs 33 words.  All threads must call.
+__device__ inline uint64_t block_excl_scan(uint64_t x, uint64_t* total, uint64_t* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    uint64_t v = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint64_t y = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += y;
+    }
+    if (lane == 31) sh[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t w = lane < nw ? sh[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint64_t y = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += y;
+        }
+        if (lane < nw) sh[lane] = w;
+        if (lane == 31) sh[32] = w;
+    }
+    __syncthreads();
+    uint64_t r = v - x + (warp > 0 ? sh[warp - 1] : 0);
+    *total = sh[32];
+    __syncthreads();
+    return r;
+}
+
+// Exclusive scan in place of a shared array of n 64-bit values; returns the sum.
+__device__ inline uint64_t smem_array_excl_scan(uint64_t* a, int n, uint64_t* sh) {
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int lo = min(n, (int)threadIdx.x * per), hi = min(n, lo + per);
+    uint64_t s = 0;
+    for (int i = lo; i < hi; ++i) s += a[i];
+    uint64_t total;
+    uint64_t run = block_excl_scan(s, &total, sh);
+    for (int i = lo; i < hi; ++i) {
+        uint64_t t = a[i];
+        a[i] = run;
+        run += t;
+    }
+    __syncthreads();
+    return total;
+}
+
+// --------------------------------------------------------------- records
+struct Rec {
+    uint64_t lo, hi;
+};
+
+__device__ __forceinline__ void rec_put(Rec& r, uint64_t val, int off) {  // val < 2^32
+    if (off < 64) {
+        r.lo |= val << off;
+        if (off > 32) r.hi |= val >> (64 - off);
+    } else {
+        r.hi |= val << (off - 64);
+    }
+}
+__device__ __forceinline__ uint32_t rec_get(const Rec& r, int off, int width) {  // width <= 32
+    uint64_t v;
+    if (off >= 64) v = r.hi >> (off - 64);
+    else if (off == 0) v = r.lo;
+    else v = (r.lo >> off) | (r.hi << (64 - off));
+    return (uint32_t)(v & ((1ull << width) - 1));
+}
+
+// ------------------------------------------------ element local edge tables
+// Edge-neighbors of local node i (the other end of each local edge at i).
+// tri: the two others; quad: the two cyclic neighbours; tet: the three others;
+// hex (VTK): the two cyclic neighbours in i's face plus the node across.
+template <int TYPE>
+struct ElemT;
+template <>
+struct ElemT<NN_TRI> {
+    static constexpr int NPE = 3, K = 2;
+    __device__ static int nbr(int i, int s) { return (i + 1 + s) % 3; }
+};
+template <>
+struct ElemT<NN_QUAD> {
+    static constexpr int NPE = 4, K = 2;
+    __device__ static int nbr(int i, int s) { return (i + (s ? 3 : 1)) & 3; }
+};
+template <>
+struct ElemT<NN_TET> {
+    static constexpr int NPE = 4, K = 3;
+    __device__ static int nbr(int i, int s) { return (i + 1 + s) & 3; }
+};
+template <>
+struct ElemT<NN_HEX> {
+    static constexpr int NPE = 8, K = 3;
+    __device__ static int nbr(int i, int s) {
+        return s == 2 ? (i ^ 4) : ((i & 4) | ((i + (s ? 3 : 1)) & 3));
+    }
+};
+
+__device__ __forceinline__ int npe_of(int t) { return t == NN_TRI ? 3 : (t == NN_HEX ? 8 : 4); }
+__device__ __forceinline__ int nbr_of(int t, int i, int s) {
+    switch (t) {
+        case NN_TRI: return ElemT<NN_TRI>::nbr(i, s);
+        case NN_QUAD: return ElemT<NN_QUAD>::nbr(i, s);
+        case NN_TET: return ElemT<NN_TET>::nbr(i, s);
+        default: return ElemT<NN_HEX>::nbr(i, s);
+    }
+}
+__device__ __forceinline__ int k_of(int t) { return (t == NN_TRI || t == NN_QUAD) ? 2 : 3; }
+
+// ----------------------------------------------------------------- sorting
+// Insertion sort of a short row (generic pointer: shared or global memory).
+__device__ inline void insertion_sort(uint32_t* a, int n) {
+    for (int i = 1; i < n; ++i) {
+        uint32_t x = a[i];
+        int j = i - 1;
+        while (j >= 0 && a[j] > x) {
+            a[j + 1] = a[j];
+            --j;
+        }
+        a[j + 1] = x;
+    }
+}
+
+// Ascending bitonic sort of a[0..n) by the whole block (generic pointer).
+// Uses the formulation in which every compare-exchange puts the minimum at
+// the lower index (first step of each merge mirrors the block), so indices
+// >= n behave as +infinity and their compare-exchanges can be skipped.
+// All threads of the block must call.
+__device__ inline void block_bitonic_sort(uint32_t* a, int64_t n) {
+    if (n < 2) return;
+    int64_t P = 1;
+    while (P < n) P <<= 1;
+    for (int64_t k = 2; k <= P; k <<= 1) {
+        for (int64_t j = k >> 1; j > 0; j >>= 1) {
+            for (int64_t t = threadIdx.x; t < (P >> 1); t += blockDim.x) {
+                int64_t idx = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+                int64_t q = (j == (k >> 1)) ? (idx ^ (k - 1)) : (idx ^ j);
+                if (q < n) {
+                    uint32_t x = a[idx], y = a[q];
+                    if (x > y) {
+                        a[idx] = y;
+                        a[q] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace nn

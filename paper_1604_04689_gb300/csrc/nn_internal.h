@@ -1,0 +1,88 @@
+// Internal host/device interface of libnn: the build plan, kernel parameter
+// blocks and the launchers defined in the kernel translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "nn.h"
+
+namespace nn {
+
+// Layout of one packed incidence record (node v is local node i of element e).
+// Bit fields, low to high:
+//   vloc   : v mod 2^sb (the record's bucket is v >> sb)            [sb bits]
+//   nf     : 1 if v already occurred earlier in e (degenerate e)   [1 bit, elems wanted]
+//   e      : element id                                            [eb bits, elems wanted]
+//   n_0..  : k edge-neighbors of v in e, stored as id+1, 0 = none  [nb bits each, nodes wanted]
+// The record is 8 bytes when the fields fit 64 bits, else 16 bytes.
+struct RecFmt {
+    int sb;
+    int want;
+    int k;
+    int off_nf, off_e, eb;
+    int off_n, nb;
+    int rb;  // 8 or 16
+};
+
+// Element walk: the kernels that read the connectivity (histogram and
+// partition passes).  Each CTA owns a fixed range of work units; a unit is 4
+// triangles (three 16-byte loads) or one element of any other type.
+struct EmitParams {
+    int type;
+    int64_t n_nodes, n_elems, n_conn;
+    const int32_t* conn;
+    const int64_t* elem_ptr;
+    const uint8_t* elem_type;
+    RecFmt fmt;
+    int64_t n_buckets;
+    int n_cta;
+    uint32_t* hist;   // [n_cta][n_buckets]: counts, then write offsets
+    uint8_t* rec;     // records, grouped by bucket
+    uint64_t rec_cap; // records that fit; more only when elem_ptr is invalid
+    int32_t* status;
+};
+
+struct OffsetsParams {
+    uint32_t* hist;
+    int n_cta;
+    int64_t n_buckets;
+    uint32_t* bstart;       // [n_buckets+1] first record of each bucket
+    uint64_t* lb_state;     // lookback words, one per tile of buckets
+    uint32_t* ticket;
+    uint64_t rec_cap;       // bucket starts are clamped to the record array
+    int32_t* status;
+};
+
+// Bucket pass: one CTA per bucket (persistent, buckets taken in order),
+// builds the rows of the bucket's 2^sb nodes and writes both CSRs.
+struct BucketParams {
+    RecFmt fmt;
+    int64_t n_nodes;
+    int64_t n_buckets;
+    const uint8_t* rec;
+    const uint32_t* bstart;
+    uint64_t* lb_n;         // lookback words, node CSR, one per bucket
+    uint64_t* lb_e;         // lookback words, element CSR, one per bucket
+    uint32_t* ticket;
+    uint32_t* spill;        // global scratch for buckets too large for shared memory
+    uint64_t spill_words;
+    unsigned long long* spill_cursor;
+    int64_t* rp_n; int32_t* col_n; int64_t cap_n;
+    int64_t* rp_e; int32_t* col_e; int64_t cap_e;
+    int32_t* status;
+    uint32_t area_words;    // shared-memory words available for tables and lists
+};
+
+constexpr int EMIT_THREADS = 1024;
+constexpr int OFFSETS_THREADS = 512;
+
+// launchers (return the CUDA error of the launch)
+cudaError_t launch_hist(const EmitParams& p, size_t smem, cudaStream_t s);
+cudaError_t launch_part(const EmitParams& p, size_t smem, cudaStream_t s);
+cudaError_t launch_offsets(const OffsetsParams& p, cudaStream_t s);
+cudaError_t launch_bucket(const BucketParams& p, int grid, int threads, size_t smem, cudaStream_t s);
+cudaError_t set_smem_limits(size_t emit_smem, size_t bucket_smem);
+
+}  // namespace nn

@@ -1,0 +1,280 @@
+"""ctypes binding of libnn.so (include/nn.h): argument marshalling only.
+
+Every step of the build runs in the CUDA kernels behind the C ABI; this
+module only turns torch device tensors into the C structs and calls it.
+PyTorch provides device memory and the stream.
+
+Low level (same names as the C ABI): ``nn_create``, ``nn_destroy``,
+``nn_query``, ``nn_neighbor_nodes``, ``nn_neighbor_elements``,
+``nn_neighbors_both``, ``nn_status_str``.
+
+High level: ``DeviceMesh`` (connectivity on the device) and ``Builder``,
+which sizes and allocates workspace and outputs with torch and returns CSR
+tensors.  If the library has not been built, loading raises RuntimeError --
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+from typing import Optional
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnn.so")
+
+TRI, QUAD, TET, HEX, MIXED = 0, 1, 2, 3, 255
+WANT_NODES, WANT_ELEMS, WANT_BOTH = 1, 2, 3
+STATUS = {0: "NN_OK", 1: "NN_ERR_ARG", 2: "NN_ERR_WORKSPACE", 3: "NN_ERR_CAPACITY", 4: "NN_ERR_NODE_RANGE",
+          5: "NN_ERR_ELEM_PTR", 6: "NN_ERR_TIMEOUT", 7: "NN_ERR_BUDGET", 8: "NN_ERR_CUDA"}
+NPE = {TRI: 3, QUAD: 4, TET: 4, HEX: 8}
+
+
+class NNMesh(C.Structure):
+    _fields_ = [("type", C.c_int32), ("n_nodes", C.c_int64), ("n_elems", C.c_int64), ("n_conn", C.c_int64),
+                ("conn", C.c_void_p), ("elem_ptr", C.c_void_p), ("elem_type", C.c_void_p)]
+
+
+class NNCSR(C.Structure):
+    _fields_ = [("row_ptr", C.c_void_p), ("col", C.c_void_p), ("col_capacity", C.c_int64)]
+
+
+class NNError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded libnn.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libnn.so not built ({LIB_PATH}); run __graft_entry__.build()")
+            L = C.CDLL(LIB_PATH)
+            P = C.c_void_p
+            L.nn_create.argtypes = [C.POINTER(P)]
+            L.nn_create.restype = C.c_int
+            L.nn_destroy.argtypes = [P]
+            L.nn_destroy.restype = None
+            L.nn_query.argtypes = [P, C.POINTER(NNMesh), C.c_int, C.POINTER(C.c_size_t),
+                                   C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+            L.nn_query.restype = C.c_int
+            for name in ("nn_neighbor_nodes", "nn_neighbor_elements"):
+                f = getattr(L, name)
+                f.argtypes = [P, C.POINTER(NNMesh), C.POINTER(NNCSR), P, C.c_size_t, P, P]
+                f.restype = C.c_int
+            L.nn_neighbors_both.argtypes = [P, C.POINTER(NNMesh), C.POINTER(NNCSR), C.POINTER(NNCSR), P,
+                                            C.c_size_t, P, P]
+            L.nn_neighbors_both.restype = C.c_int
+            L.nn_profile_enable.argtypes = [P, C.c_int]
+            L.nn_profile_enable.restype = C.c_int
+            L.nn_profile_read.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]
+            L.nn_profile_read.restype = C.c_int
+            L.nn_plan_info.argtypes = [P, C.POINTER(NNMesh), C.c_int, C.POINTER(C.c_int64), C.c_int]
+            L.nn_plan_info.restype = C.c_int
+            L.nn_status_str.argtypes = [C.c_int]
+            L.nn_status_str.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------ C ABI mirrors
+
+def nn_create() -> int:
+    h = C.c_void_p()
+    st = lib().nn_create(C.byref(h))
+    if st:
+        raise NNError(st, "nn_create")
+    return h.value
+
+
+def nn_destroy(h: int) -> None:
+    lib().nn_destroy(h)
+
+
+def nn_query(h: int, mesh: NNMesh, want: int):
+    ws = C.c_size_t()
+    nc = C.c_int64()
+    ec = C.c_int64()
+    st = lib().nn_query(h, C.byref(mesh), want, C.byref(ws), C.byref(nc), C.byref(ec))
+    if st:
+        raise NNError(st, "nn_query")
+    return ws.value, nc.value, ec.value
+
+
+PLAN_KEYS = ("sb", "n_buckets", "emit_ctas", "record_bytes", "ws_min", "bucket_ctas")
+
+
+def nn_plan_info(h: int, mesh: NNMesh, want: int) -> dict:
+    info = (C.c_int64 * 6)()
+    st = lib().nn_plan_info(h, C.byref(mesh), want, info, 6)
+    if st:
+        raise NNError(st, "nn_plan_info")
+    return dict(zip(PLAN_KEYS, list(info)))
+
+
+def nn_neighbor_nodes(h, mesh: NNMesh, out: NNCSR, ws: int, ws_bytes: int, d_status: int, stream: int) -> int:
+    return lib().nn_neighbor_nodes(h, C.byref(mesh), C.byref(out), ws, ws_bytes, d_status, stream)
+
+
+def nn_neighbor_elements(h, mesh: NNMesh, out: NNCSR, ws: int, ws_bytes: int, d_status: int, stream: int) -> int:
+    return lib().nn_neighbor_elements(h, C.byref(mesh), C.byref(out), ws, ws_bytes, d_status, stream)
+
+
+def nn_neighbors_both(h, mesh: NNMesh, nodes: NNCSR, elems: NNCSR, ws: int, ws_bytes: int, d_status: int,
+                      stream: int) -> int:
+    return lib().nn_neighbors_both(h, C.byref(mesh), C.byref(nodes), C.byref(elems), ws, ws_bytes, d_status,
+                                   stream)
+
+
+STAGES = ("init", "hist", "offsets", "part", "bucket")
+
+
+def nn_profile_enable(h: int, enable: bool) -> None:
+    st = lib().nn_profile_enable(h, int(enable))
+    if st:
+        raise NNError(st, "nn_profile_enable")
+
+
+def nn_profile_read(h: int):
+    """({stage: summed ms}, calls) since profiling was enabled."""
+    ms = (C.c_double * 5)()
+    calls = C.c_int64()
+    st = lib().nn_profile_read(h, ms, C.byref(calls), 5)
+    if st:
+        raise NNError(st, "nn_profile_read")
+    return dict(zip(STAGES, list(ms))), calls.value
+
+
+def nn_status_str(code: int) -> str:
+    return lib().nn_status_str(code).decode()
+
+
+# -------------------------------------------------------------- high level
+
+@dataclass
+class DeviceMesh:
+    """Connectivity resident on the device (torch tensors)."""
+    etype: int
+    n_nodes: int
+    conn: "torch.Tensor"                        # int32, 16-byte aligned
+    elem_ptr: Optional["torch.Tensor"] = None   # int64, MIXED only
+    elem_type: Optional["torch.Tensor"] = None  # uint8, MIXED only
+
+    @property
+    def n_conn(self) -> int:
+        return int(self.conn.numel())
+
+    @property
+    def n_elems(self) -> int:
+        if self.etype == MIXED:
+            return int(self.elem_type.numel())
+        return self.n_conn // NPE[self.etype]
+
+    def struct(self) -> NNMesh:
+        def ptr(t):
+            return t.data_ptr() if t is not None and t.numel() else None
+        return NNMesh(self.etype, self.n_nodes, self.n_elems, self.n_conn, ptr(self.conn), ptr(self.elem_ptr),
+                      ptr(self.elem_type))
+
+    @staticmethod
+    def from_host(mesh, device="cuda", pin: bool = False) -> "DeviceMesh":
+        """Copy a host mesh (e.g. meshgen.Mesh) to the device."""
+        import torch
+
+        def to(a):
+            if a is None:
+                return None
+            t = torch.from_numpy(a)
+            if pin:
+                t = t.pin_memory()
+            return t.to(device, non_blocking=pin)
+        return DeviceMesh(int(mesh.etype), int(mesh.n_nodes), to(mesh.conn), to(mesh.elem_ptr), to(mesh.elem_type))
+
+
+class Builder:
+    """Owns a handle, a workspace and output buffers; rebuilds on demand."""
+
+    def __init__(self, device=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(self.device):
+            self.h = nn_create()
+        self.ws = None
+        self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
+
+    def close(self):
+        if self.h:
+            nn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def query(self, dm: DeviceMesh, want: int):
+        return nn_query(self.h, dm.struct(), want)
+
+    def workspace(self, nbytes: int):
+        if self.ws is None or self.ws.numel() < nbytes:
+            self.ws = self.torch.empty(max(nbytes, 256), dtype=self.torch.uint8, device=self.device)
+        return self.ws
+
+    def alloc_outputs(self, dm: DeviceMesh, want: int, node_cap=None, elem_cap=None):
+        torch = self.torch
+        _, nc, ec = self.query(dm, want)
+        out = {}
+        if want & WANT_NODES:
+            out["nodes"] = (torch.empty(dm.n_nodes + 1, dtype=torch.int64, device=self.device),
+                            torch.empty(max(nc if node_cap is None else node_cap, 1), dtype=torch.int32,
+                                        device=self.device))
+        if want & WANT_ELEMS:
+            out["elems"] = (torch.empty(dm.n_nodes + 1, dtype=torch.int64, device=self.device),
+                            torch.empty(max(ec if elem_cap is None else elem_cap, 1), dtype=torch.int32,
+                                        device=self.device))
+        return out
+
+    def launch(self, dm: DeviceMesh, want: int, out: dict, ws=None, ws_bytes=None, stream=None) -> int:
+        """Enqueue one build (no sync).  Returns the host status code."""
+        torch = self.torch
+        if ws is None:
+            nbytes, _, _ = self.query(dm, want)
+            ws = self.workspace(nbytes)
+            ws_bytes = nbytes
+        s = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        mesh = dm.struct()
+
+        def csr(pair):
+            rp, col = pair
+            return NNCSR(rp.data_ptr(), col.data_ptr(), col.numel())
+        if want == WANT_NODES:
+            return nn_neighbor_nodes(self.h, mesh, csr(out["nodes"]), ws.data_ptr(), ws_bytes,
+                                     self.status.data_ptr(), s)
+        if want == WANT_ELEMS:
+            return nn_neighbor_elements(self.h, mesh, csr(out["elems"]), ws.data_ptr(), ws_bytes,
+                                        self.status.data_ptr(), s)
+        return nn_neighbors_both(self.h, mesh, csr(out["nodes"]), csr(out["elems"]), ws.data_ptr(), ws_bytes,
+                                 self.status.data_ptr(), s)
+
+    def build(self, dm: DeviceMesh, want: int = WANT_BOTH):
+        """Build and return {'status': int, 'nodes': (row_ptr, col), 'elems': (row_ptr, col)} (col trimmed)."""
+        out = self.alloc_outputs(dm, want)
+        st = self.launch(dm, want, out)
+        if st:
+            raise NNError(st, "launch")
+        self.torch.cuda.synchronize(self.device)
+        res = {"status": int(self.status.item())}
+        for k, (rp, col) in out.items():
+            nnz = int(rp[-1].item()) if res["status"] == 0 else col.numel()
+            res[k] = (rp, col[:nnz])
+        return res
