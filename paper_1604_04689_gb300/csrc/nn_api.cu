@@ -19,8 +19,8 @@ struct nn_handle {
     int device = 0;
     int sms = 0;
     size_t smem_optin = 0;     // max dynamic shared memory per block
-    size_t bucket_smem = 0;    // dynamic shared memory of the bucket kernel
-    int bucket_blocks_per_sm = 1;
+    size_t bucket_smem = 0;    // largest dynamic shared memory of the bucket kernel
+    size_t smem_per_sm = 0;
     int sb_override = -1;      // fixed bucket width (tests / tuning), -1 = automatic
     // per-stage timing (nn_profile_*)
     bool prof = false;
@@ -53,11 +53,13 @@ struct Plan {
     RecFmt fmt{};
     int64_t B = 0;
     int G = 1;
+    int G_part = 1;
     size_t emit_smem = 0;
-    size_t off_hist = 0, off_bstart = 0, off_rec = 0, off_lb_off = 0, off_lb_n = 0, off_lb_e = 0,
+    size_t off_hist = 0, off_bstart = 0, off_gcur = 0, off_rec = 0, off_lb_off = 0, off_lb_n = 0, off_lb_e = 0,
            off_ctrl = 0, off_spill = 0, zero_begin = 0, zero_end = 0;
     size_t ws_min = 0, ws_rec = 0;
     int bucket_grid = 0;
+    size_t bucket_smem = 0;
     uint32_t area_words = 0;
 };
 
@@ -98,23 +100,34 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
         while (Tt <= std::ceil(C)) Tt *= 2;
     }
     const double per_node = 4.0 * (E + Tt + 0.5 * C);  // list + table + staged row, bytes
-    int sb = SB_MIN;
-    for (int s = SB_MAX; s >= SB_MIN; --s) {
-        const double area = (double)h->bucket_smem - (double)BUCKET_FIXED_PER_NODE * (1 << s) - BUCKET_FIXED;
-        if (area > 0 && (double)(1 << s) * per_node <= 0.6 * area) {
-            sb = s;
-            break;
+    // prefer a shared-memory size that lets two bucket CTAs share an SM, so one
+    // CTA's barriers and lookback waits overlap the other's memory traffic
+    int sb = -1;
+    size_t bsmem = std::min(h->bucket_smem, h->smem_per_sm / 2 - 1024);
+    for (int pass = 0; pass < 2 && sb < 0; ++pass) {
+        if (pass == 1) bsmem = h->bucket_smem;
+        for (int s = SB_MAX; s >= SB_MIN + 2; --s) {
+            const double area = (double)bsmem - (double)BUCKET_FIXED_PER_NODE * (1 << s) - BUCKET_FIXED;
+            if (area > 0 && (double)(1 << s) * per_node <= 0.6 * area) {
+                sb = s;
+                break;
+            }
         }
     }
-    if (h->sb_override >= SB_MIN && h->sb_override <= SB_MAX) sb = h->sb_override;
+    if (sb < 0) sb = SB_MIN;
+    if (h->sb_override >= SB_MIN && h->sb_override <= SB_MAX) {
+        sb = h->sb_override;
+        bsmem = h->bucket_smem;
+    }
+    p.bucket_smem = bsmem;
     // the bucket kernel's per-node arrays must leave room for its list/table area
     auto fixed_of = [](int s) { return BUCKET_FIXED_PER_NODE * ((size_t)1 << s) + BUCKET_FIXED; };
     const size_t min_area = 4096 * 4;
-    while (sb > SB_MIN && fixed_of(sb) + min_area > h->bucket_smem) --sb;
+    while (sb > SB_MIN && fixed_of(sb) + min_area > p.bucket_smem) --sb;
     const int64_t B_max = (int64_t)((h->smem_optin - 1024) / 4);
     auto nbk = [&](int s) { return (p.N + (1ll << s) - 1) >> s; };
     while (nbk(sb) > B_max && sb < SB_MAX) ++sb;
-    if (nbk(sb) > B_max || fixed_of(sb) + min_area > h->bucket_smem) return NN_ERR_ARG;
+    if (nbk(sb) > B_max || fixed_of(sb) + min_area > p.bucket_smem) return NN_ERR_ARG;
     p.B = nbk(sb);
 
     RecFmt& f = p.fmt;
@@ -136,11 +149,13 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     p.emit_smem = std::max<size_t>(16, (size_t)p.B * 4);
     const int cps = p.emit_smem + 2048 <= 113 * 1024 ? 2 : 1;
     p.G = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sms * cps, (n_units + 2047) / 2048));
+    p.G_part = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sms * 2, (n_units + 511) / 512));
 
     // workspace layout
     size_t o = 0;
     p.off_hist = o; o = align_up(o + (size_t)p.G * p.B * 4);
     p.off_bstart = o; o = align_up(o + ((size_t)p.B + 1) * 4);
+    p.off_gcur = o; o = align_up(o + (size_t)p.B * 4);
     p.off_rec = o; o = align_up(o + (size_t)p.n_conn * f.rb);
     p.zero_begin = o;
     p.off_lb_off = o; o = align_up(o + (size_t)((p.B + OFFSETS_THREADS - 1) / OFFSETS_THREADS) * 8 + 8);
@@ -154,8 +169,10 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     p.ws_rec = o + spill;
 
     const size_t fixed = BUCKET_FIXED_PER_NODE * ((size_t)1 << sb) + BUCKET_FIXED;
-    p.area_words = (uint32_t)((h->bucket_smem - fixed) / 4);
-    p.bucket_grid = (int)std::min<int64_t>(p.B, (int64_t)h->sms * h->bucket_blocks_per_sm);
+    p.area_words = (uint32_t)((p.bucket_smem - fixed) / 4);
+    int per_sm = 1;
+    if (bucket_occupancy(&per_sm, bucket_threads(), p.bucket_smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+    p.bucket_grid = (int)std::min<int64_t>(p.B, (int64_t)h->sms * per_sm);
     *P = p;
     return NN_OK;
 }
@@ -213,7 +230,9 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
     ep.fmt = p.fmt;
     ep.n_buckets = p.B;
     ep.n_cta = p.G;
+    ep.n_cta_part = p.G_part;
     ep.hist = reinterpret_cast<uint32_t*>(w + p.off_hist);
+    ep.gcur = reinterpret_cast<uint32_t*>(w + p.off_gcur);
     ep.rec = w + p.off_rec;
     ep.rec_cap = (uint64_t)p.n_conn;
     ep.status = d_status;
@@ -223,6 +242,7 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
     op.n_cta = p.G;
     op.n_buckets = p.B;
     op.bstart = reinterpret_cast<uint32_t*>(w + p.off_bstart);
+    op.gcur = ep.gcur;
     op.lb_state = reinterpret_cast<uint64_t*>(w + p.off_lb_off);
     op.ticket = ctrl + 0;
     op.rec_cap = (uint64_t)p.n_conn;
@@ -258,9 +278,9 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
     prof_mark(h, 2, s);
     if (launch_offsets(op, s) != cudaSuccess) return NN_ERR_CUDA;
     prof_mark(h, 3, s);
-    if (launch_part(ep, p.emit_smem, s) != cudaSuccess) return NN_ERR_CUDA;
+    if (launch_part(ep, s) != cudaSuccess) return NN_ERR_CUDA;
     prof_mark(h, 4, s);
-    if (launch_bucket(bp, p.bucket_grid, bucket_threads(), h->bucket_smem, s) != cudaSuccess)
+    if (launch_bucket(bp, p.bucket_grid, bucket_threads(), p.bucket_smem, s) != cudaSuccess)
         return NN_ERR_CUDA;
     prof_mark(h, 5, s);
     if (h->prof) h->pending = true;
@@ -275,14 +295,16 @@ nn_status nn_create(nn_handle** out) {
     if (!out) return NN_ERR_ARG;
     nn_handle* h = new (std::nothrow) nn_handle();
     if (!h) return NN_ERR_ARG;
-    int optin = 0;
+    int optin = 0, per_sm = 0;
     if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess) {
         delete h;
         return NN_ERR_CUDA;
     }
     h->smem_optin = (size_t)optin;
+    h->smem_per_sm = (size_t)per_sm;
     h->bucket_smem = h->smem_optin;
     if (const char* e = std::getenv("NN_SB")) h->sb_override = std::atoi(e);
     if (const char* e = std::getenv("NN_BUCKET_SMEM_KB")) {
@@ -293,9 +315,6 @@ nn_status nn_create(nn_handle** out) {
         delete h;
         return NN_ERR_CUDA;
     }
-    int blocks = 0;
-    if (bucket_occupancy(&blocks, bucket_threads(), h->bucket_smem) != cudaSuccess || blocks < 1) blocks = 1;
-    h->bucket_blocks_per_sm = blocks;
     *out = h;
     return NN_OK;
 }

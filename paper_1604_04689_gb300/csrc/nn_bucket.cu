@@ -23,6 +23,8 @@ namespace {
 
 constexpr int BUCKET_THREADS = 512;
 constexpr int LONG_ROW = 48;  // rows longer than this are sorted by the whole block
+constexpr int UNROLL = 2;     // records loaded per thread before they are used
+constexpr uint32_t RANK_MAX = 64;  // rows up to this length are sorted by ranking
 
 template <int RB>
 __device__ __forceinline__ Rec load_rec(const uint8_t* base, uint32_t r) {
@@ -58,6 +60,18 @@ __device__ __forceinline__ bool tab_insert(uint32_t* tab, uint32_t mask, int shi
     return false;
 }
 
+// Row of entry i: the largest l with off[l] <= i (off is a non-decreasing
+// exclusive scan with off[0] = 0, so empty rows are skipped).
+__device__ __forceinline__ int row_of(const uint32_t* off, int n, uint32_t i) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= i) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo - 1;
+}
+
 __device__ __forceinline__ uint32_t table_size(uint32_t c) {
     if (c == 0) return 0;
     uint32_t t = 2;
@@ -66,7 +80,7 @@ __device__ __forceinline__ uint32_t table_size(uint32_t c) {
 }
 
 template <int RB, int K>
-__global__ void __launch_bounds__(BUCKET_THREADS) k_bucket(BucketParams p) {
+__global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
     extern __shared__ __align__(16) uint8_t smem[];
     const RecFmt f = p.fmt;
     const int NB = 1 << f.sb;
@@ -83,12 +97,27 @@ __global__ void __launch_bounds__(BUCKET_THREADS) k_bucket(BucketParams p) {
     const bool want_n = f.want & NN_WANT_NODES, want_e = f.want & NN_WANT_ELEMS;
     const int tid = threadIdx.x, BS = blockDim.x;
 
+    if (tid == 0) misc[0] = atomicAdd(p.ticket, 1u);
+    __syncthreads();
+    int64_t b_next = (int64_t)misc[0];
+    __syncthreads();
     for (;;) {
-        if (tid == 0) misc[0] = atomicAdd(p.ticket, 1u);
-        __syncthreads();
-        const int64_t b = (int64_t)misc[0];
-        __syncthreads();
+        const int64_t b = b_next;
         if (b >= p.n_buckets) break;
+        // take the next bucket now and start pulling its records into L2
+        if (tid == 0) {
+            const uint32_t nx = atomicAdd(p.ticket, 1u);
+            misc[5] = nx;
+            if (nx < p.n_buckets) {
+                uint64_t lo = (uint64_t)p.bstart[nx] * RB, hi = (uint64_t)p.bstart[nx + 1] * RB;
+                lo &= ~15ull;
+                hi = (hi + 15) & ~15ull;  // the record array is padded to 256 bytes
+                for (uint64_t a = lo; a < hi; a += 32768) {
+                    const uint32_t n = (uint32_t)(hi - a < 32768ull ? hi - a : 32768ull);
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p.rec + a), "r"(n) : "memory");
+                }
+            }
+        }
         const int64_t v0 = b << f.sb;
         const int nb = (int)(p.n_nodes - v0 < (int64_t)NB ? p.n_nodes - v0 : (int64_t)NB);
         const uint32_t r0 = p.bstart[b], r1 = p.bstart[b + 1];
@@ -96,16 +125,24 @@ __global__ void __launch_bounds__(BUCKET_THREADS) k_bucket(BucketParams p) {
         // counts per node: element entries (high word) and candidates (low word)
         for (int l = tid; l < NB; l += BS) cnt[l] = 0;
         __syncthreads();
-        for (uint32_t r = r0 + tid; r < r1; r += BS) {
-            Rec x = load_rec<RB>(p.rec, r);
-            const uint32_t vloc = (uint32_t)x.lo & vmask;
-            uint64_t inc = 0;
-            if (want_e && !rec_get(x, f.off_nf, 1)) inc += 1ull << 32;
-            if (want_n) {
+        for (uint32_t r = r0 + tid; r < r1; r += UNROLL * BS) {
+            Rec xs[UNROLL];
 #pragma unroll
-                for (int s = 0; s < K; ++s) inc += rec_get(x, f.off_n + s * f.nb, f.nb) != 0;
+            for (int q = 0; q < UNROLL; ++q)
+                if (r + q * BS < r1) xs[q] = load_rec<RB>(p.rec, r + q * BS);
+#pragma unroll
+            for (int q = 0; q < UNROLL; ++q) {
+                if (r + q * BS >= r1) break;
+                const Rec& x = xs[q];
+                const uint32_t vloc = (uint32_t)x.lo & vmask;
+                uint64_t inc = 0;
+                if (want_e && !rec_get(x, f.off_nf, 1)) inc += 1ull << 32;
+                if (want_n) {
+#pragma unroll
+                    for (int s = 0; s < K; ++s) inc += rec_get(x, f.off_n + s * f.nb, f.nb) != 0;
+                }
+                if (inc) atomicAdd(reinterpret_cast<unsigned long long*>(&cnt[vloc]), (unsigned long long)inc);
             }
-            if (inc) atomicAdd(reinterpret_cast<unsigned long long*>(&cnt[vloc]), (unsigned long long)inc);
         }
         __syncthreads();
         // element offsets
@@ -125,9 +162,14 @@ __global__ void __launch_bounds__(BUCKET_THREADS) k_bucket(BucketParams p) {
         __syncthreads();
         const uint64_t Tb = smem_array_excl_scan(cnt, NB, sh_scan);
         for (int l = tid; l < NB; l += BS) toff[l] = (uint32_t)cnt[l];
+        const bool fast_b = Eb + Tb <= p.area_words;
+        if (want_e && tid == 0) lb_publish(p.lb_e, b, Eb);
+        if (tid < 32) {  // large buckets write element lists straight to the output: need the offset now
+            const uint64_t ge = (want_e && !fast_b) ? lb_resolve(p.lb_e, b, Eb, p.status) : 0;
+            if (tid == 0) misc[1] = ge;
+        }
         if (tid == 0) {
-            misc[1] = want_e ? lookback(p.lb_e, b, Eb, p.status) : 0;
-            const bool fast = Eb + Tb <= p.area_words;
+            const bool fast = fast_b;
             uint64_t spill_off = 0;
             bool tab_ok = true;
             if (!fast && want_n && Tb > 0) {
@@ -139,12 +181,11 @@ __global__ void __launch_bounds__(BUCKET_THREADS) k_bucket(BucketParams p) {
             }
             misc[2] = spill_off;
             misc[4] = (fast ? 1 : 0) | (tab_ok ? 2 : 0);
-            if (want_e && misc[1] + Eb > (uint64_t)p.cap_e) set_status(p.status, NN_ERR_CAPACITY);
         }
         __syncthreads();
-        const uint64_t Ge = misc[1];
+        uint64_t Ge = misc[1];
         const bool fast = misc[4] & 1, tab_ok = (misc[4] & 2) && want_n;
-        const bool e_ok = want_e && Ge + Eb <= (uint64_t)p.cap_e;
+        bool e_ok = want_e && Ge + Eb <= (uint64_t)p.cap_e;  // final for large buckets, rechecked below
         uint32_t* elist = fast ? area : reinterpret_cast<uint32_t*>(p.col_e) + Ge;
         const bool e_write = want_e && (fast || e_ok);
         uint32_t* tab = fast ? area + Eb : p.spill + misc[2];
@@ -153,8 +194,15 @@ __global__ void __launch_bounds__(BUCKET_THREADS) k_bucket(BucketParams p) {
         __syncthreads();
 
         // second pass: element lists and neighbour tables
-        for (uint32_t r = r0 + tid; r < r1; r += BS) {
-            Rec x = load_rec<RB>(p.rec, r);
+        for (uint32_t r = r0 + tid; r < r1; r += UNROLL * BS) {
+          Rec xs[UNROLL];
+#pragma unroll
+          for (int q = 0; q < UNROLL; ++q)
+              if (r + q * BS < r1) xs[q] = load_rec<RB>(p.rec, r + q * BS);
+#pragma unroll
+          for (int q = 0; q < UNROLL; ++q) {
+            if (r + q * BS >= r1) break;
+            const Rec& x = xs[q];
             const uint32_t vloc = (uint32_t)x.lo & vmask;
             if (e_write && !rec_get(x, f.off_nf, 1)) {
                 const uint32_t q = atomicAdd(&aux[vloc], 1u);
@@ -170,66 +218,159 @@ __global__ void __launch_bounds__(BUCKET_THREADS) k_bucket(BucketParams p) {
                     if (y && tab_insert(t, T - 1, shift, y - 1, p.status)) atomicAdd(&ucnt[vloc], 1u);
                 }
             }
+          }
         }
         __syncthreads();
         for (int l = tid; l < NB; l += BS) cnt[l] = ucnt[l];
         __syncthreads();
         const uint64_t Ub = smem_array_excl_scan(cnt, NB, sh_scan);
         for (int l = tid; l < NB; l += BS) aux[l] = (uint32_t)cnt[l];
-        if (tid == 0) {
-            misc[3] = want_n ? lookback(p.lb_n, b, Ub, p.status) : 0;
-            if (want_n && misc[3] + Ub > (uint64_t)p.cap_n) set_status(p.status, NN_ERR_CAPACITY);
-        }
-        __syncthreads();
-        const uint64_t Gn = misc[3];
-        const bool n_ok = tab_ok && Gn + Ub <= (uint64_t)p.cap_n;
-
-        // row pointers
-        for (int l = tid; l < nb; l += BS) {
-            if (want_n) p.rp_n[v0 + l] = (int64_t)(Gn + aux[l]);
-            if (want_e) p.rp_e[v0 + l] = (int64_t)(Ge + eoff[l]);
-        }
-        if (b == p.n_buckets - 1 && tid == 0) {
-            if (want_n) p.rp_n[p.n_nodes] = (int64_t)(Gn + Ub);
-            if (want_e) p.rp_e[p.n_nodes] = (int64_t)(Ge + Eb);
-        }
+        if (want_n && tid == 0) lb_publish(p.lb_n, b, Ub);
+        uint64_t Gn = 0;
+        bool n_ok = false;
+        // output offsets of this bucket: resolved now for large buckets (they
+        // write straight to the output), at the very end for the others, when
+        // the predecessors have long published
+        auto resolve = [&](bool elem_too) {
+            if (tid < 32) {
+                const uint64_t gn = want_n ? lb_resolve(p.lb_n, b, Ub, p.status) : 0;
+                const uint64_t ge = (want_e && elem_too) ? lb_resolve(p.lb_e, b, Eb, p.status) : misc[1];
+                if (tid == 0) {
+                    misc[3] = gn;
+                    misc[1] = ge;
+                    if (want_n && gn + Ub > (uint64_t)p.cap_n) set_status(p.status, NN_ERR_CAPACITY);
+                    if (want_e && ge + Eb > (uint64_t)p.cap_e) set_status(p.status, NN_ERR_CAPACITY);
+                }
+            }
+            __syncthreads();
+            Gn = misc[3];
+            Ge = misc[1];
+            n_ok = tab_ok && Gn + Ub <= (uint64_t)p.cap_n;
+            e_ok = want_e && Ge + Eb <= (uint64_t)p.cap_e;
+            for (int l = tid; l < nb; l += BS) {
+                if (want_n) p.rp_n[v0 + l] = (int64_t)(Gn + aux[l]);
+                if (want_e) p.rp_e[v0 + l] = (int64_t)(Ge + eoff[l]);
+            }
+            if (b == p.n_buckets - 1 && tid == 0) {
+                if (want_n) p.rp_n[p.n_nodes] = (int64_t)(Gn + Ub);
+                if (want_e) p.rp_e[p.n_nodes] = (int64_t)(Ge + Eb);
+            }
+        };
 
         // rows: gather each node's distinct neighbours from its table, sort
         uint32_t* stage = (fast && Eb + Tb + Ub <= p.area_words) ? area + Eb + Tb : nullptr;
-        uint32_t* dst_n = stage ? stage : reinterpret_cast<uint32_t*>(p.col_n) + Gn;
-        if (n_ok) {
-            for (int l = tid; l < NB; l += BS) {
-                const uint32_t U = ucnt[l];
-                if (U == 0) continue;
-                uint32_t* d = dst_n + aux[l];
-                const uint32_t* t = tab + toff[l];
-                uint32_t j = 0;
-                for (uint32_t s = 0; s < tsz[l]; ++s) {
-                    const uint32_t y = t[s];
-                    if (y != EMPTY) d[j++] = y;
+        uint32_t* sorted = nullptr;
+        if (stage) {
+            if (Ub + Eb <= Tb) sorted = tab;  // the tables are dead once gathered
+            else if (Eb + Tb + 2 * Ub + Eb <= p.area_words) sorted = stage + Ub;
+        }
+        if (sorted) {
+            // gather: four threads per node, starting at bank-staggered slots
+            uint32_t* fill = reinterpret_cast<uint32_t*>(cnt);
+            for (int l = tid; l < NB; l += BS) fill[l] = 0;
+            __syncthreads();
+            if (tab_ok) {
+                for (int idx = tid; idx < NB * 4; idx += BS) {
+                    const int l = idx >> 2;
+                    const uint32_t T = tsz[l];
+                    const uint32_t* t = tab + toff[l];
+                    const uint32_t dst = aux[l], st = 4u * (uint32_t)l;
+                    for (uint32_t q = idx & 3; q < T; q += 4) {
+                        const uint32_t y = t[(q + st) & (T - 1)];
+                        if (y != EMPTY) stage[dst + atomicAdd(&fill[l], 1u)] = y;
+                    }
                 }
-                if (U <= LONG_ROW) insertion_sort(d, (int)U);
             }
-        }
-        if (e_write) {
-            for (int l = tid; l < NB; l += BS) {
-                const uint32_t E = (l + 1 < NB ? eoff[l + 1] : (uint32_t)Eb) - eoff[l];
-                if (E > 1 && E <= LONG_ROW) insertion_sort(elist + eoff[l], (int)E);
+            __syncthreads();
+            // sort each row by rank (every entry counts the smaller entries of its row)
+            int has_long = 0;
+            uint32_t* sorted_e = sorted + Ub;
+            if (tab_ok) {
+                for (uint32_t i = tid; i < Ub; i += BS) {
+                    const int l = row_of(aux, NB, i);
+                    const uint32_t a = aux[l], U = ucnt[l], x = stage[i];
+                    uint32_t rank = i - a;
+                    if (U <= RANK_MAX) {
+                        rank = 0;
+                        for (uint32_t j = a; j < a + U; ++j) rank += stage[j] < x;
+                    } else {
+                        has_long = 1;
+                    }
+                    sorted[a + rank] = x;
+                }
             }
-        }
-        __syncthreads();
-        for (int l = 0; l < NB; ++l) {  // uniform loop: long rows, whole block
-            if (n_ok && ucnt[l] > LONG_ROW) block_bitonic_sort(dst_n + aux[l], ucnt[l]);
+            if (want_e) {
+                for (uint32_t i = tid; i < Eb; i += BS) {
+                    const int l = row_of(eoff, NB, i);
+                    const uint32_t a = eoff[l], E = (l + 1 < NB ? eoff[l + 1] : (uint32_t)Eb) - a, x = elist[i];
+                    uint32_t rank = i - a;
+                    if (E <= RANK_MAX) {
+                        rank = 0;
+                        for (uint32_t j = a; j < a + E; ++j) rank += elist[j] < x;
+                    } else {
+                        has_long = 1;
+                    }
+                    sorted_e[a + rank] = x;
+                }
+            }
+            has_long = __syncthreads_or(has_long);
+            for (int l = 0; has_long && l < NB; ++l) {  // uniform loop: long rows, whole block
+                if (tab_ok && ucnt[l] > RANK_MAX) block_bitonic_sort(sorted + aux[l], ucnt[l]);
+                if (want_e) {
+                    const uint32_t E = (l + 1 < NB ? eoff[l + 1] : (uint32_t)Eb) - eoff[l];
+                    if (E > RANK_MAX) block_bitonic_sort(sorted_e + eoff[l], E);
+                }
+            }
+            resolve(true);
+            if (n_ok)
+                for (uint64_t i = tid; i < Ub; i += BS) p.col_n[Gn + i] = (int32_t)sorted[i];
+            if (e_ok)
+                for (uint64_t i = tid; i < Eb; i += BS) p.col_e[Ge + i] = (int32_t)sorted_e[i];
+            __syncthreads();
+        } else {
+            // large buckets: one thread per node, rows in global memory or staged
+            resolve(fast);
+            uint32_t* dst_n = stage ? stage : reinterpret_cast<uint32_t*>(p.col_n) + Gn;
+            int has_long = 0;
+            if (n_ok) {
+                for (int l = tid; l < NB; l += BS) {
+                    const uint32_t U = ucnt[l];
+                    if (U == 0) continue;
+                    has_long |= U > LONG_ROW;
+                    uint32_t* d = dst_n + aux[l];
+                    const uint32_t* t = tab + toff[l];
+                    const uint32_t T = tsz[l];
+                    uint32_t j = 0;
+                    for (uint32_t q = 0; q < T; ++q) {
+                        const uint32_t y = t[(q + (uint32_t)l) & (T - 1)];
+                        if (y != EMPTY) d[j++] = y;
+                    }
+                    if (U <= LONG_ROW) insertion_sort(d, (int)U);
+                }
+            }
             if (e_write) {
-                const uint32_t E = (l + 1 < NB ? eoff[l + 1] : (uint32_t)Eb) - eoff[l];
-                if (E > LONG_ROW) block_bitonic_sort(elist + eoff[l], E);
+                for (int l = tid; l < NB; l += BS) {
+                    const uint32_t E = (l + 1 < NB ? eoff[l + 1] : (uint32_t)Eb) - eoff[l];
+                    has_long |= E > LONG_ROW;
+                    if (E > 1 && E <= LONG_ROW) insertion_sort(elist + eoff[l], (int)E);
+                }
             }
+            has_long = __syncthreads_or(has_long);
+            for (int l = 0; has_long && l < NB; ++l) {  // uniform loop: long rows, whole block
+                if (n_ok && ucnt[l] > LONG_ROW) block_bitonic_sort(dst_n + aux[l], ucnt[l]);
+                if (e_write) {
+                    const uint32_t E = (l + 1 < NB ? eoff[l + 1] : (uint32_t)Eb) - eoff[l];
+                    if (E > LONG_ROW) block_bitonic_sort(elist + eoff[l], E);
+                }
+            }
+            __syncthreads();
+            if (stage && n_ok)
+                for (uint64_t i = tid; i < Ub; i += BS) p.col_n[Gn + i] = (int32_t)stage[i];
+            if (fast && e_ok)
+                for (uint64_t i = tid; i < Eb; i += BS) p.col_e[Ge + i] = (int32_t)elist[i];
+            __syncthreads();
         }
-        __syncthreads();
-        if (stage && n_ok)
-            for (uint64_t i = tid; i < Ub; i += BS) p.col_n[Gn + i] = (int32_t)stage[i];
-        if (fast && e_ok)
-            for (uint64_t i = tid; i < Eb; i += BS) p.col_e[Ge + i] = (int32_t)elist[i];
+        b_next = (int64_t)misc[5];
         __syncthreads();
     }
 }

@@ -72,6 +72,60 @@ __device__ inline uint64_t lookback(uint64_t* state, uint64_t t, uint64_t agg, i
     return excl;
 }
 
+// Warp-parallel lookback in two halves.  lb_publish (one thread) makes the
+// tile's aggregate visible as soon as it is known; lb_resolve (all 32 lanes
+// of one warp, possibly much later) walks back over the predecessors, 32 at
+// a time, consuming the ready ones nearest to t and stopping at the first
+// inclusive prefix, then publishes t's inclusive prefix.  Only the nearest
+// not-yet-ready predecessor is ever waited for.
+__device__ __forceinline__ void lb_publish(uint64_t* state, uint64_t t, uint64_t agg) {
+    st_release(&state[t], (t == 0 ? LB_INC : LB_AGG) | agg);
+}
+
+__device__ inline uint64_t lb_resolve(uint64_t* state, uint64_t t, uint64_t agg, int32_t* status) {
+    const int lane = threadIdx.x & 31;
+    if (t == 0) return 0;
+    uint64_t excl = 0;
+    int64_t p = (int64_t)t - 1;
+    uint64_t t0 = 0;
+    for (;;) {
+        const int64_t idx = p - lane;
+        const uint64_t s = idx >= 0 ? ld_acquire(&state[idx]) : LB_INC;  // before tile 0: inclusive zero
+        const unsigned not_ready = __ballot_sync(0xffffffffu, (s >> 62) == 0);
+        const int k = not_ready ? __ffs(not_ready) - 1 : 32;  // lanes 0..k-1 are ready
+        const unsigned ready_mask = k == 32 ? 0xffffffffu : ((1u << k) - 1);
+        const unsigned inc = __ballot_sync(0xffffffffu, (s >> 62) == 2) & ready_mask;
+        const int stop = inc ? __ffs(inc) - 1 : k - 1;
+        uint64_t v = lane <= stop ? (s & LB_VAL) : 0;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+        excl += v;
+        if (inc) break;
+        p -= k;
+        if (k == 0) {  // nearest predecessor not ready yet: bounded wait
+            const uint64_t now = global_ns();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > WAIT_LIMIT_NS) {
+                if (lane == 0) set_status(status, NN_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(100);
+        } else {
+            t0 = 0;
+        }
+    }
+    if (lane == 0) st_release(&state[t], LB_INC | ((excl + agg) & LB_VAL));
+    __syncwarp();
+    return excl;
+}
+
+__device__ inline uint64_t warp_lookback(uint64_t* state, uint64_t t, uint64_t agg, int32_t* status) {
+    if ((threadIdx.x & 31) == 0) lb_publish(state, t, agg);
+    __syncwarp();
+    return lb_resolve(state, t, agg, status);
+}
+
 // ------------------------------------------------------------ block scans
 // Exclusive scan of one 64-bit value per thread; *total gets the block sum.
 // `sh` needs 33 words.  All threads must call.

@@ -4,10 +4,12 @@
 // integer pairs and then sorts them by key.  Here the pairs of one node never
 // leave a packed per-incidence record (node, element, the node's edge
 // neighbours in that element), and records are partitioned by node range
-// ("bucket") instead of sorted: a histogram pass and a partition pass over
-// the connectivity, each CTA owning a fixed slice of elements and keeping its
-// per-bucket counters in shared memory, so the only random global traffic is
-// one vector store per incidence into a bucket's write head.
+// ("bucket") instead of sorted: a histogram pass over the connectivity (each
+// CTA owns a fixed slice of elements and counts into shared memory), a scan
+// of the bucket totals, and a partition pass that appends every record to
+// its bucket through one cursor per bucket, so the random global traffic is
+// one L2 atomic and one vector store per incidence, and the partially filled
+// sectors at the buckets' write heads (one per bucket) stay resident in L2.
 #include "nn_device.cuh"
 
 namespace nn {
@@ -57,7 +59,7 @@ template <int TYPE, class F>
 __device__ __forceinline__ void walk_cta(const EmitParams& p, F&& f) {
     constexpr int UNIT = TYPE == NN_TRI ? 4 : 1;
     const int64_t n_units = (p.n_elems + UNIT - 1) / UNIT;
-    const int64_t u0 = n_units * blockIdx.x / p.n_cta, u1 = n_units * (blockIdx.x + 1) / p.n_cta;
+    const int64_t u0 = n_units * blockIdx.x / gridDim.x, u1 = n_units * (blockIdx.x + 1) / gridDim.x;
     for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
         if constexpr (TYPE == NN_TRI) {
             const int64_t e0 = u * 4;
@@ -113,39 +115,149 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_hist(EmitParams p) {
     for (int64_t b = threadIdx.x; b < B; b += blockDim.x) row[b] = sh_hist[b];
 }
 
+// Load one work unit (4 triangles or one element); returns the runtime type
+// (the element's own type for mixed meshes) and sets ok[w] for each valid
+// element of the unit.  Invalid elements raise the status and are skipped.
+template <int TYPE>
+__device__ __forceinline__ int load_unit(const EmitParams& p, int64_t u, int32_t* nd, bool* ok) {
+    if constexpr (TYPE == NN_TRI) {
+        const int64_t e0 = u * 4;
+        if (e0 + 4 <= p.n_elems) {
+            const int4* c4 = reinterpret_cast<const int4*>(p.conn + e0 * 3);
+            int4 a = __ldg(c4), b = __ldg(c4 + 1), c = __ldg(c4 + 2);
+            nd[0] = a.x; nd[1] = a.y; nd[2] = a.z; nd[3] = a.w;
+            nd[4] = b.x; nd[5] = b.y; nd[6] = b.z; nd[7] = b.w;
+            nd[8] = c.x; nd[9] = c.y; nd[10] = c.z; nd[11] = c.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 12; ++q) nd[q] = (e0 * 3 + q < p.n_conn) ? __ldg(p.conn + e0 * 3 + q) : 0;
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            bool v = e0 + w < p.n_elems;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) v = v && nd[3 * w + i] >= 0 && (int64_t)nd[3 * w + i] < p.n_nodes;
+            if (!v && e0 + w < p.n_elems) set_status(p.status, NN_ERR_NODE_RANGE);
+            ok[w] = v;
+        }
+        return NN_TRI;
+    } else if constexpr (TYPE == NN_MIXED) {
+        const int t = __ldg(p.elem_type + u);
+        const int64_t a = __ldg(p.elem_ptr + u), b = __ldg(p.elem_ptr + u + 1);
+        if (t > NN_HEX || a < 0 || b > p.n_conn || b - a != npe_of(t)) {
+            set_status(p.status, NN_ERR_ELEM_PTR);
+            ok[0] = false;
+            return NN_HEX;
+        }
+        const int npe = (int)(b - a);
+        bool v = true;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            nd[q] = q < npe ? __ldg(p.conn + a + q) : 0;
+            if (q < npe) v = v && nd[q] >= 0 && (int64_t)nd[q] < p.n_nodes;
+        }
+        if (!v) set_status(p.status, NN_ERR_NODE_RANGE);
+        ok[0] = v;
+        return t;
+    } else {
+        constexpr int NPE = ElemT<TYPE>::NPE;
+        const int4* c4 = reinterpret_cast<const int4*>(p.conn) + (NPE / 4) * u;
+        int4 a = __ldg(c4);
+        nd[0] = a.x; nd[1] = a.y; nd[2] = a.z; nd[3] = a.w;
+        if constexpr (NPE == 8) {
+            int4 b = __ldg(c4 + 1);
+            nd[4] = b.x; nd[5] = b.y; nd[6] = b.z; nd[7] = b.w;
+        }
+        bool v = true;
+#pragma unroll
+        for (int i = 0; i < NPE; ++i) v = v && nd[i] >= 0 && (int64_t)nd[i] < p.n_nodes;
+        if (!v) set_status(p.status, NN_ERR_NODE_RANGE);
+        ok[0] = v;
+        return TYPE;
+    }
+}
+
+// Partition pass.  A thread takes UPT consecutive work units and issues all
+// their cursor atomics before writing any record, so it keeps 8-16 L2
+// atomics in flight (the pass is bound by atomic latency, not bandwidth).
+template <int TYPE>
+struct PartShape {
+    static constexpr int UNIT = TYPE == NN_TRI ? 4 : 1;
+    static constexpr int NPE = TYPE == NN_MIXED ? 8 : ElemT<(TYPE == NN_MIXED ? NN_HEX : TYPE)>::NPE;
+    static constexpr int UPT = (TYPE == NN_TRI) ? 1 : (NPE == 8 ? 2 : 3);  // units per thread per round
+};
+
 template <int TYPE, int RB>
-__global__ void __launch_bounds__(EMIT_THREADS) k_part(EmitParams p) {
-    extern __shared__ uint32_t sh_cur[];
-    const int64_t B = p.n_buckets;
-    const uint32_t* row = p.hist + (int64_t)blockIdx.x * B;
-    for (int64_t b = threadIdx.x; b < B; b += blockDim.x) sh_cur[b] = row[b];
-    __syncthreads();
+__global__ void __launch_bounds__(PART_THREADS, 2) k_part(EmitParams p) {
+    using S = PartShape<TYPE>;
+    constexpr int UNIT = S::UNIT, NPE = S::NPE, UPT = S::UPT, NI = NPE * UNIT;
     const RecFmt f = p.fmt;
     const uint32_t vmask = (1u << f.sb) - 1;
-    walk_cta<TYPE>(p, [&](int32_t v, int nf, int64_t e, int32_t x0, int32_t x1, int32_t x2) {
-        const uint32_t pos = atomicAdd(&sh_cur[v >> f.sb], 1u);
-        Rec r{(uint64_t)((uint32_t)v & vmask), 0};
-        if (f.want & NN_WANT_ELEMS) {
-            rec_put(r, (uint64_t)nf, f.off_nf);
-            rec_put(r, (uint64_t)e, f.off_e);
+    const int64_t n_units = (p.n_elems + UNIT - 1) / UNIT;
+    const int64_t u0 = n_units * blockIdx.x / gridDim.x, u1 = n_units * (blockIdx.x + 1) / gridDim.x;
+    for (int64_t ub = u0 + (int64_t)threadIdx.x * UPT; ub < u1; ub += (int64_t)blockDim.x * UPT) {
+        int32_t nd[UPT][NI];
+        bool ok[UPT][UNIT];
+        int t[UPT];
+        uint32_t pos[UPT][NI];
+#pragma unroll
+        for (int k = 0; k < UPT; ++k) {
+#pragma unroll
+            for (int w = 0; w < UNIT; ++w) ok[k][w] = false;
+            t[k] = TYPE == NN_MIXED ? NN_HEX : TYPE;
+            if (ub + k < u1) t[k] = load_unit<TYPE>(p, ub + k, nd[k], ok[k]);
         }
-        if (f.want & NN_WANT_NODES) {
-            rec_put(r, (uint64_t)(uint32_t)(x0 + 1), f.off_n);
-            rec_put(r, (uint64_t)(uint32_t)(x1 + 1), f.off_n + f.nb);
-            if (f.k > 2) rec_put(r, (uint64_t)(uint32_t)(x2 + 1), f.off_n + 2 * f.nb);
+#pragma unroll
+        for (int k = 0; k < UPT; ++k) {
+            const int npe = TYPE == NN_MIXED ? npe_of(t[k]) : NPE;
+#pragma unroll
+            for (int j = 0; j < NI; ++j) {
+                const int w = j / NPE, i = j % NPE;
+                pos[k][j] = 0xFFFFFFFFu;
+                if (ok[k][w] && i < npe) pos[k][j] = atomicAdd(&p.gcur[(uint32_t)nd[k][j] >> f.sb], 1u);
+            }
         }
-        if (pos >= p.rec_cap) return;  // only with overlapping (invalid) mixed elements
-        if constexpr (RB == 8) {
-            reinterpret_cast<uint64_t*>(p.rec)[pos] = r.lo;
-        } else {
-            reinterpret_cast<ulonglong2*>(p.rec)[pos] = make_ulonglong2(r.lo, r.hi);
+#pragma unroll
+        for (int k = 0; k < UPT; ++k) {
+            const int tk = t[k];
+#pragma unroll
+            for (int j = 0; j < NI; ++j) {
+                const int w = j / NPE, i = j % NPE;
+                if (pos[k][j] >= p.rec_cap) continue;  // not an incidence, or overlapping invalid mixed elements
+                const int32_t* e_nd = nd[k] + w * NPE;
+                const int32_t v = e_nd[i];
+                int nf = 0;
+#pragma unroll
+                for (int q = 0; q < NPE; ++q) nf |= (q < i) && (e_nd[q] == v);
+                const int K = TYPE == NN_MIXED ? k_of(tk) : ElemT<(TYPE == NN_MIXED ? NN_HEX : TYPE)>::K;
+                Rec r{(uint64_t)((uint32_t)v & vmask), 0};
+                if (f.want & NN_WANT_ELEMS) {
+                    rec_put(r, (uint64_t)nf, f.off_nf);
+                    rec_put(r, (uint64_t)((ub + k) * UNIT + w), f.off_e);
+                }
+                if (f.want & NN_WANT_NODES) {
+#pragma unroll
+                    for (int s = 0; s < 3; ++s) {
+                        if (s >= K) break;
+                        const int li = TYPE == NN_MIXED ? nbr_of(tk, i, s)
+                                                        : ElemT<(TYPE == NN_MIXED ? NN_HEX : TYPE)>::nbr(i, s);
+                        const int32_t y = e_nd[li];
+                        rec_put(r, y == v ? 0ull : (uint64_t)(uint32_t)(y + 1), f.off_n + s * f.nb);
+                    }
+                }
+                if constexpr (RB == 8) {
+                    reinterpret_cast<uint64_t*>(p.rec)[pos[k][j]] = r.lo;
+                } else {
+                    reinterpret_cast<ulonglong2*>(p.rec)[pos[k][j]] = make_ulonglong2(r.lo, r.hi);
+                }
+            }
         }
-    });
+    }
 }
 
 // Per bucket b: total records = sum over CTAs of hist[c][b]; bucket starts by
-// a lookback scan over tiles of buckets; then each CTA's write offset inside
-// the bucket (CTA order, so a bucket's records are grouped by element slice).
+// a lookback scan over tiles of buckets; each bucket's write cursor starts at
+// its start.
 __global__ void __launch_bounds__(OFFSETS_THREADS) k_offsets(OffsetsParams p) {
     __shared__ uint64_t sh_scan[33];
     __shared__ uint32_t sh_tile;
@@ -160,17 +272,16 @@ __global__ void __launch_bounds__(OFFSETS_THREADS) k_offsets(OffsetsParams p) {
         for (int c = 0; c < p.n_cta; ++c) tot += p.hist[(int64_t)c * B + b];
     uint64_t agg;
     uint64_t ex = block_excl_scan(tot, &agg, sh_scan);
-    if (threadIdx.x == 0) sh_base = lookback(p.lb_state, tile, agg, p.status);
+    if (threadIdx.x < 32) {
+        const uint64_t base = warp_lookback(p.lb_state, tile, agg, p.status);
+        if (threadIdx.x == 0) sh_base = base;
+    }
     __syncthreads();
     if (b < B) {
-        uint64_t run = sh_base + ex;
+        const uint64_t run = sh_base + ex;
         p.bstart[b] = (uint32_t)min(run, p.rec_cap);
-        for (int c = 0; c < p.n_cta; ++c) {
-            uint32_t t = p.hist[(int64_t)c * B + b];
-            p.hist[(int64_t)c * B + b] = (uint32_t)min(run, p.rec_cap);
-            run += t;
-        }
-        if (b == B - 1) p.bstart[B] = (uint32_t)min(run, p.rec_cap);
+        p.gcur[b] = (uint32_t)min(run, p.rec_cap);
+        if (b == B - 1) p.bstart[B] = (uint32_t)min(run + tot, p.rec_cap);
     }
 }
 
@@ -180,20 +291,15 @@ cudaError_t hist_t(const EmitParams& p, size_t smem, cudaStream_t s) {
     return cudaGetLastError();
 }
 template <int TYPE>
-cudaError_t part_t(const EmitParams& p, size_t smem, cudaStream_t s) {
-    if (p.fmt.rb == 8) k_part<TYPE, 8><<<p.n_cta, EMIT_THREADS, smem, s>>>(p);
-    else k_part<TYPE, 16><<<p.n_cta, EMIT_THREADS, smem, s>>>(p);
+cudaError_t part_t(const EmitParams& p, cudaStream_t s) {
+    if (p.fmt.rb == 8) k_part<TYPE, 8><<<p.n_cta_part, PART_THREADS, 0, s>>>(p);
+    else k_part<TYPE, 16><<<p.n_cta_part, PART_THREADS, 0, s>>>(p);
     return cudaGetLastError();
 }
 
 template <int TYPE>
 cudaError_t set_emit_smem(size_t bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_hist<TYPE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_part<TYPE, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_part<TYPE, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    return e;
+    return cudaFuncSetAttribute(k_hist<TYPE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 }  // namespace
@@ -208,13 +314,13 @@ cudaError_t launch_hist(const EmitParams& p, size_t smem, cudaStream_t s) {
     }
 }
 
-cudaError_t launch_part(const EmitParams& p, size_t smem, cudaStream_t s) {
+cudaError_t launch_part(const EmitParams& p, cudaStream_t s) {
     switch (p.type) {
-        case NN_TRI: return part_t<NN_TRI>(p, smem, s);
-        case NN_QUAD: return part_t<NN_QUAD>(p, smem, s);
-        case NN_TET: return part_t<NN_TET>(p, smem, s);
-        case NN_HEX: return part_t<NN_HEX>(p, smem, s);
-        default: return part_t<NN_MIXED>(p, smem, s);
+        case NN_TRI: return part_t<NN_TRI>(p, s);
+        case NN_QUAD: return part_t<NN_QUAD>(p, s);
+        case NN_TET: return part_t<NN_TET>(p, s);
+        case NN_HEX: return part_t<NN_HEX>(p, s);
+        default: return part_t<NN_MIXED>(p, s);
     }
 }
 

@@ -37,8 +37,10 @@ struct EmitParams {
     const uint8_t* elem_type;
     RecFmt fmt;
     int64_t n_buckets;
-    int n_cta;
-    uint32_t* hist;   // [n_cta][n_buckets]: counts, then write offsets
+    int n_cta;        // CTAs of the histogram pass (rows of hist)
+    int n_cta_part;   // CTAs of the partition pass
+    uint32_t* hist;   // [n_cta][n_buckets] record counts of each CTA's element slice
+    uint32_t* gcur;   // [n_buckets] write cursor of each bucket (starts at the bucket start)
     uint8_t* rec;     // records, grouped by bucket
     uint64_t rec_cap; // records that fit; more only when elem_ptr is invalid
     int32_t* status;
@@ -49,6 +51,7 @@ struct OffsetsParams {
     int n_cta;
     int64_t n_buckets;
     uint32_t* bstart;       // [n_buckets+1] first record of each bucket
+    uint32_t* gcur;         // [n_buckets] set to the bucket starts
     uint64_t* lb_state;     // lookback words, one per tile of buckets
     uint32_t* ticket;
     uint64_t rec_cap;       // bucket starts are clamped to the record array
@@ -76,11 +79,12 @@ struct BucketParams {
 };
 
 constexpr int EMIT_THREADS = 1024;
-constexpr int OFFSETS_THREADS = 512;
+constexpr int PART_THREADS = 512;
+constexpr int OFFSETS_THREADS = 128;
 
 // launchers (return the CUDA error of the launch)
 cudaError_t launch_hist(const EmitParams& p, size_t smem, cudaStream_t s);
-cudaError_t launch_part(const EmitParams& p, size_t smem, cudaStream_t s);
+cudaError_t launch_part(const EmitParams& p, cudaStream_t s);
 cudaError_t launch_offsets(const OffsetsParams& p, cudaStream_t s);
 cudaError_t launch_bucket(const BucketParams& p, int grid, int threads, size_t smem, cudaStream_t s);
 cudaError_t set_smem_limits(size_t emit_smem, size_t bucket_smem);
