@@ -136,6 +136,25 @@ nn_status nn_neighbors_both(nn_handle* h, const nn_mesh* mesh, nn_csr* nodes, nn
 nn_status nn_profile_enable(nn_handle* h, int enable);
 nn_status nn_profile_read(nn_handle* h, double* ms, int64_t* calls, int n_stages);
 
+/* Allocation-free build of both results, for callers that may not allocate
+ * device memory (code that runs inside an application owning all device
+ * memory through its own pool, or a loop that must never enter the CUDA
+ * allocator).  The paper has no counterpart: it is a deployment variant of
+ * nn_neighbors_both.  Instead of a caller workspace it uses one scratch array
+ * of NN_NOALLOC_SCRATCH_BYTES that the library keeps in device memory; every
+ * GPU that loads libnn holds that array until the process exits.  The caller
+ * still passes the mesh, both output CSRs and d_status (all device memory it
+ * owns) and the stream.  The first call on a device (with that device
+ * current) looks up the array's device address; make that first call before
+ * any stream capture.  Meshes whose build needs more scratch than the array
+ * holds (roughly 1.5 million node-element incidences) are rejected with
+ * NN_ERR_WORKSPACE before anything is enqueued.  All calls share the array
+ * and it keeps the last call's contents: calls whose work overlaps on the GPU
+ * race, so the caller must serialise them (one stream, or events). */
+#define NN_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+nn_status nn_neighbors_both_noalloc(const nn_mesh* mesh, nn_csr* nodes, nn_csr* elems, int32_t* d_status,
+                                    nn_stream_t stream);
+
 /* Short English text for a status code (static storage). */
 const char* nn_status_str(nn_status s);
 

@@ -289,6 +289,28 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
 
 }  // namespace
 
+namespace nn {
+
+// Build with a handle described by plain device limits (no handle object on
+// the heap): used by the allocation-free entry point.
+nn_status build_with_limits(int sms, size_t smem_optin, size_t smem_per_sm, const nn_mesh* m, int want,
+                            nn_csr* nodes, nn_csr* elems, void* ws, size_t ws_bytes, int32_t* d_status,
+                            cudaStream_t s, size_t* ws_min) {
+    nn_handle h;
+    h.sms = sms;
+    h.smem_optin = smem_optin;
+    h.smem_per_sm = smem_per_sm;
+    h.bucket_smem = smem_optin;
+    Plan p;
+    nn_status st = make_plan(&h, m, want, &p);
+    if (st != NN_OK) return st;
+    if (ws_min) *ws_min = p.ws_min;
+    if (p.ws_min > ws_bytes) return NN_ERR_WORKSPACE;
+    return run(&h, m, want, nodes, elems, ws, ws_bytes, d_status, s);
+}
+
+}  // namespace nn
+
 extern "C" {
 
 nn_status nn_create(nn_handle** out) {

@@ -87,6 +87,10 @@ cudaError_t launch_hist(const EmitParams& p, size_t smem, cudaStream_t s);
 cudaError_t launch_part(const EmitParams& p, cudaStream_t s);
 cudaError_t launch_offsets(const OffsetsParams& p, cudaStream_t s);
 cudaError_t launch_bucket(const BucketParams& p, int grid, int threads, size_t smem, cudaStream_t s);
-cudaError_t set_smem_limits(size_t emit_smem, size_t bucket_smem);
+cudaError_t set_emit_smem_all(size_t bytes);
+cudaError_t set_bucket_smem_all(size_t bytes);
+nn_status build_with_limits(int sms, size_t smem_optin, size_t smem_per_sm, const nn_mesh* m, int want,
+                            nn_csr* nodes, nn_csr* elems, void* ws, size_t ws_bytes, int32_t* d_status,
+                            cudaStream_t s, size_t* ws_min);
 
 }  // namespace nn

@@ -79,6 +79,8 @@ def lib():
             L.nn_profile_read.restype = C.c_int
             L.nn_plan_info.argtypes = [P, C.POINTER(NNMesh), C.c_int, C.POINTER(C.c_int64), C.c_int]
             L.nn_plan_info.restype = C.c_int
+            L.nn_neighbors_both_noalloc.argtypes = [C.POINTER(NNMesh), C.POINTER(NNCSR), C.POINTER(NNCSR), P, P]
+            L.nn_neighbors_both_noalloc.restype = C.c_int
             L.nn_status_str.argtypes = [C.c_int]
             L.nn_status_str.restype = C.c_char_p
             _lib = L
@@ -132,6 +134,14 @@ def nn_neighbors_both(h, mesh: NNMesh, nodes: NNCSR, elems: NNCSR, ws: int, ws_b
                       stream: int) -> int:
     return lib().nn_neighbors_both(h, C.byref(mesh), C.byref(nodes), C.byref(elems), ws, ws_bytes, d_status,
                                    stream)
+
+
+NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def nn_neighbors_both_noalloc(mesh: NNMesh, nodes: NNCSR, elems: NNCSR, d_status: int, stream: int) -> int:
+    """Both CSRs with the library's fixed device scratch instead of a workspace (allocates nothing)."""
+    return lib().nn_neighbors_both_noalloc(C.byref(mesh), C.byref(nodes), C.byref(elems), d_status, stream)
 
 
 STAGES = ("init", "hist", "offsets", "part", "bucket")
