@@ -126,6 +126,43 @@ nn_status nn_neighbor_elements(nn_handle* h, const nn_mesh* mesh, nn_csr* out, v
 nn_status nn_neighbors_both(nn_handle* h, const nn_mesh* mesh, nn_csr* nodes, nn_csr* elems,
                             void* ws, size_t ws_bytes, int32_t* d_status, nn_stream_t stream);
 
+/* ------------------------------------------------------------- batches
+ * Many meshes of any types, each with its own outputs, built by ONE launch
+ * sequence (batch init, histogram, offsets, partition, bucket pass) over the
+ * disjoint union of the meshes: every mesh owns a contiguous range of node
+ * buckets and its CSRs are mesh-local (row_ptr from 0, local node and element
+ * ids).  The batch's description is written by nn_batch_prepare into HOST
+ * staging memory that the caller owns (pinned, so the copy is asynchronous
+ * and can be captured), and nn_batch_launch copies it to the workspace and
+ * enqueues the kernels, whose grids depend only on the capacities: one CUDA
+ * graph captured around nn_batch_launch replays for every batch prepared into
+ * the same staging buffer with the same capacities and workspace.
+ * Results equal those of nn_neighbors_both on each mesh alone. */
+typedef struct {
+    int32_t max_meshes;  /* meshes per batch                                      */
+    int32_t want;        /* NN_WANT_*                                             */
+    int64_t max_elems;   /* elements of all meshes of a batch                     */
+    int64_t max_nodes;   /* nodes of all meshes of a batch                        */
+    int64_t max_conn;    /* connectivity entries of all meshes of a batch         */
+    int32_t sb;          /* log2 of the bucket width in nodes (0 = default, 4..11) */
+} nn_batch_caps;
+
+/* Sizes for a capacity: workspace bytes (device) and staging bytes (host). */
+nn_status nn_batch_query(nn_handle* h, const nn_batch_caps* caps, size_t* ws_bytes, size_t* staging_bytes);
+
+/* Host only: validate the meshes and write the batch description into
+ * `staging`.  node_out / elem_out are arrays of n_meshes CSRs (either may be
+ * NULL if not wanted); d_status is a device array of n_meshes status words
+ * (mesh m's device-detected errors go to d_status[m]).  The caller must not
+ * rewrite `staging` while a launch that reads it may still be pending. */
+nn_status nn_batch_prepare(nn_handle* h, const nn_batch_caps* caps, const nn_mesh* meshes,
+                           const nn_csr* node_out, const nn_csr* elem_out, int32_t* d_status, int n_meshes,
+                           void* staging, size_t staging_bytes);
+
+/* Enqueue the batch described in `staging` on `stream` (no host sync). */
+nn_status nn_batch_launch(nn_handle* h, const nn_batch_caps* caps, const void* staging, void* ws,
+                          size_t ws_bytes, nn_stream_t stream);
+
 /* Per-stage device timing (used by the benchmark).  While enabled, compute
  * calls record CUDA events on their stream between their stages:
  *   0 workspace/status init, 1 bucket histogram, 2 bucket offsets,

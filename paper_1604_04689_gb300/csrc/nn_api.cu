@@ -287,6 +287,190 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
     return NN_OK;
 }
 
+// --------------------------------------------------------------- batches
+
+struct BatchPlan {
+    int sb = 7;
+    int64_t B_cap = 0;
+    size_t hdr_bytes = 0, meshes_off = 0, elem_off_off = 0, bucket_off_off = 0, table_bytes = 0;
+    size_t off_bcount = 0, off_bstart = 0, off_gcur = 0, off_rec = 0, off_lb_off = 0, off_lb_n = 0,
+           off_lb_e = 0, off_ctrl = 0, off_spill = 0, ws_min = 0, ws_rec = 0;
+    size_t bucket_smem = 0;
+    uint32_t area_words = 0;
+    int bucket_grid = 0, emit_grid = 0;
+    int64_t tiles_cap = 0;
+};
+
+nn_status batch_plan(const nn_handle* h, const nn_batch_caps* c, BatchPlan* out) {
+    if (!h || !c || c->max_meshes < 1 || c->max_elems < 0 || c->max_nodes < 0 || c->max_conn < 0 ||
+        c->want < 1 || c->want > 3)
+        return NN_ERR_ARG;
+    if (c->max_conn >= (1ll << 31) || c->max_elems >= (1ll << 31)) return NN_ERR_ARG;
+    BatchPlan p;
+    p.sb = c->sb ? c->sb : 7;
+    if (p.sb < SB_MIN || p.sb > SB_MAX) return NN_ERR_ARG;
+    p.B_cap = (c->max_nodes >> p.sb) + c->max_meshes + 1;
+    p.hdr_bytes = align_up(sizeof(BatchHeader));
+    p.meshes_off = p.hdr_bytes;
+    p.elem_off_off = p.meshes_off + align_up((size_t)c->max_meshes * sizeof(BatchMesh));
+    p.bucket_off_off = p.elem_off_off + align_up(((size_t)c->max_meshes + 1) * 8);
+    p.table_bytes = p.bucket_off_off + align_up(((size_t)c->max_meshes + 1) * 8);
+    size_t o = p.table_bytes;
+    p.off_bcount = o; o = align_up(o + (size_t)p.B_cap * 4);
+    p.off_bstart = o; o = align_up(o + ((size_t)p.B_cap + 1) * 4);
+    p.off_gcur = o; o = align_up(o + (size_t)p.B_cap * 4);
+    p.off_rec = o; o = align_up(o + (size_t)c->max_conn * 16);
+    p.tiles_cap = (p.B_cap + OFFSETS_THREADS - 1) / OFFSETS_THREADS;
+    p.off_lb_off = o; o = align_up(o + ((size_t)p.tiles_cap + 1) * 8);
+    p.off_lb_n = o; o = align_up(o + (size_t)p.B_cap * 8);
+    p.off_lb_e = o; o = align_up(o + (size_t)p.B_cap * 8);
+    p.off_ctrl = o; o = align_up(o + 64);
+    p.off_spill = o;
+    p.ws_min = o;
+    p.ws_rec = o + (((size_t)16 << 20) + (size_t)c->max_conn * 8);
+    // shared memory: two CTAs per SM for narrow buckets, else one
+    const size_t fixed = BUCKET_FIXED_PER_NODE * ((size_t)1 << p.sb) + BUCKET_FIXED;
+    p.bucket_smem = p.sb <= 7 ? std::min(h->bucket_smem, h->smem_per_sm / 2 - 1024) : h->bucket_smem;
+    if (fixed + 4096 * 4 > p.bucket_smem) p.bucket_smem = h->bucket_smem;
+    if (fixed + 4096 * 4 > p.bucket_smem) return NN_ERR_ARG;
+    p.area_words = (uint32_t)((p.bucket_smem - fixed) / 4);
+    int per_sm = 1;
+    if (bucket_occupancy(&per_sm, bucket_threads(), p.bucket_smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+    p.bucket_grid = h->sms * per_sm;
+    p.emit_grid = h->sms * (2048 / batch_threads());
+    *out = p;
+    return NN_OK;
+}
+
+nn_status batch_prepare(nn_handle* h, const nn_batch_caps* c, const nn_mesh* meshes, const nn_csr* node_out,
+                        const nn_csr* elem_out, int32_t* d_status, int n, void* staging, size_t staging_bytes) {
+    BatchPlan bp;
+    nn_status st = batch_plan(h, c, &bp);
+    if (st != NN_OK) return st;
+    if (n < 0 || n > c->max_meshes || !staging || staging_bytes < bp.table_bytes || (n > 0 && (!meshes || !d_status)))
+        return NN_ERR_ARG;
+    if ((c->want & NN_WANT_NODES) && n > 0 && !node_out) return NN_ERR_ARG;
+    if ((c->want & NN_WANT_ELEMS) && n > 0 && !elem_out) return NN_ERR_ARG;
+    uint8_t* sg = static_cast<uint8_t*>(staging);
+    BatchHeader* hdr = reinterpret_cast<BatchHeader*>(sg);
+    BatchMesh* bm = reinterpret_cast<BatchMesh*>(sg + bp.meshes_off);
+    int64_t* eoff = reinterpret_cast<int64_t*>(sg + bp.elem_off_off);
+    int64_t* boff = reinterpret_cast<int64_t*>(sg + bp.bucket_off_off);
+    int64_t E = 0, Bk = 0, C = 0, Nn = 0, maxT = 0, maxN = 0;
+    for (int m = 0; m < n; ++m) {
+        const nn_mesh& M = meshes[m];
+        if ((st = check_mesh(&M)) != NN_OK) return st;
+        BatchMesh& d = bm[m];
+        d = BatchMesh{};
+        d.type = M.type;
+        d.k = (M.type == NN_TRI || M.type == NN_QUAD) ? 2 : 3;
+        d.n_nodes = M.n_nodes;
+        d.n_elems = M.n_elems;
+        d.n_conn = M.n_conn;
+        d.conn = M.conn;
+        d.elem_ptr = M.elem_ptr;
+        d.elem_type = M.elem_type;
+        if (c->want & NN_WANT_NODES) {
+            const nn_csr& o = node_out[m];
+            if (!o.row_ptr || o.col_capacity < 0 || (o.col_capacity > 0 && !o.col)) return NN_ERR_ARG;
+            d.rp_n = o.row_ptr; d.col_n = o.col; d.cap_n = o.col_capacity;
+        }
+        if (c->want & NN_WANT_ELEMS) {
+            const nn_csr& o = elem_out[m];
+            if (!o.row_ptr || o.col_capacity < 0 || (o.col_capacity > 0 && !o.col)) return NN_ERR_ARG;
+            d.rp_e = o.row_ptr; d.col_e = o.col; d.cap_e = o.col_capacity;
+        }
+        d.status = d_status + m;
+        eoff[m] = E;
+        boff[m] = Bk;
+        E += M.n_elems;
+        Bk += (M.n_nodes + (1ll << bp.sb) - 1) >> bp.sb;
+        C += M.n_conn;
+        Nn += M.n_nodes;
+        maxT = std::max<int64_t>(maxT, M.n_elems);
+        maxN = std::max<int64_t>(maxN, M.n_nodes);
+    }
+    eoff[n] = E;
+    boff[n] = Bk;
+    if (E > c->max_elems || C > c->max_conn || Nn > c->max_nodes || Bk > bp.B_cap) return NN_ERR_BUDGET;
+    RecFmt f{};
+    f.sb = bp.sb;
+    f.want = c->want;
+    f.k = 3;
+    f.eb = bits_for(maxT > 0 ? (uint64_t)(maxT - 1) : 0);
+    f.nb = bits_for((uint64_t)maxN);
+    f.off_nf = f.sb;
+    f.off_e = f.sb + 1;
+    f.off_n = (c->want & NN_WANT_ELEMS) ? f.sb + 1 + f.eb : f.sb;
+    const int total = (c->want & NN_WANT_NODES) ? f.off_n + 3 * f.nb : f.sb + 1 + f.eb;
+    if (total > 128) return NN_ERR_ARG;
+    f.rb = 16;
+    hdr->fmt = f;
+    hdr->n_meshes = n;
+    hdr->n_elems = E;
+    hdr->n_buckets = Bk;
+    hdr->n_records = C;
+    return NN_OK;
+}
+
+nn_status batch_launch(nn_handle* h, const nn_batch_caps* c, const void* staging, void* ws, size_t ws_bytes,
+                       cudaStream_t s) {
+    BatchPlan bp;
+    nn_status st = batch_plan(h, c, &bp);
+    if (st != NN_OK) return st;
+    if (!staging || !ws || (reinterpret_cast<uintptr_t>(ws) & (ALIGN - 1))) return NN_ERR_ARG;
+    if (ws_bytes < bp.ws_min) return NN_ERR_WORKSPACE;
+    uint8_t* w = static_cast<uint8_t*>(ws);
+    if (cudaMemcpyAsync(w, staging, bp.table_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return NN_ERR_CUDA;
+    BatchTables bt;
+    bt.hdr = reinterpret_cast<const BatchHeader*>(w);
+    bt.meshes = reinterpret_cast<const BatchMesh*>(w + bp.meshes_off);
+    bt.elem_off = reinterpret_cast<const int64_t*>(w + bp.elem_off_off);
+    bt.bucket_off = reinterpret_cast<const int64_t*>(w + bp.bucket_off_off);
+    uint32_t* bcount = reinterpret_cast<uint32_t*>(w + bp.off_bcount);
+    uint32_t* gcur = reinterpret_cast<uint32_t*>(w + bp.off_gcur);
+    uint32_t* ctrl = reinterpret_cast<uint32_t*>(w + bp.off_ctrl);
+    uint64_t* lb_off = reinterpret_cast<uint64_t*>(w + bp.off_lb_off);
+    uint64_t* lb_n = reinterpret_cast<uint64_t*>(w + bp.off_lb_n);
+    uint64_t* lb_e = reinterpret_cast<uint64_t*>(w + bp.off_lb_e);
+    uint8_t* rec = w + bp.off_rec;
+    if (launch_batch_emit(bt, bcount, gcur, rec, lb_off, lb_n, lb_e, ctrl, bp.emit_grid, 0, s) != cudaSuccess)
+        return NN_ERR_CUDA;
+    if (launch_batch_emit(bt, bcount, gcur, rec, lb_off, lb_n, lb_e, ctrl, bp.emit_grid, 1, s) != cudaSuccess)
+        return NN_ERR_CUDA;
+    OffsetsParams op{};
+    op.hist = bcount;
+    op.n_cta = 1;
+    op.n_buckets = bp.B_cap;
+    op.bstart = reinterpret_cast<uint32_t*>(w + bp.off_bstart);
+    op.gcur = gcur;
+    op.lb_state = lb_off;
+    op.ticket = ctrl + 0;
+    op.rec_cap = (uint64_t)c->max_conn;
+    op.status = reinterpret_cast<int32_t*>(ctrl + 8);  // passed on to every mesh by the bucket pass
+    op.hdr = bt.hdr;
+    if (launch_offsets(op, s) != cudaSuccess) return NN_ERR_CUDA;
+    if (launch_batch_emit(bt, bcount, gcur, rec, lb_off, lb_n, lb_e, ctrl, bp.emit_grid, 2, s) != cudaSuccess)
+        return NN_ERR_CUDA;
+    BucketParams kp{};
+    kp.n_buckets = 0;
+    kp.rec = rec;
+    kp.bstart = op.bstart;
+    kp.lb_n = lb_n;
+    kp.lb_e = lb_e;
+    kp.ticket = ctrl + 1;
+    kp.spill_cursor = reinterpret_cast<unsigned long long*>(ctrl + 2);
+    kp.spill = reinterpret_cast<uint32_t*>(w + bp.off_spill);
+    kp.spill_words = ws_bytes > bp.off_spill ? (ws_bytes - bp.off_spill) / 4 : 0;
+    kp.area_words = bp.area_words;
+    kp.batch = bt;
+    kp.batch_err = reinterpret_cast<const int32_t*>(ctrl + 8);
+    kp.fmt.rb = 16;
+    kp.fmt.k = 3;
+    if (launch_bucket(kp, bp.bucket_grid, bucket_threads(), bp.bucket_smem, s) != cudaSuccess) return NN_ERR_CUDA;
+    return NN_OK;
+}
+
 }  // namespace
 
 namespace nn {
@@ -300,7 +484,7 @@ nn_status build_with_limits(int sms, size_t smem_optin, size_t smem_per_sm, cons
     h.sms = sms;
     h.smem_optin = smem_optin;
     h.smem_per_sm = smem_per_sm;
-    h.bucket_smem = smem_optin;
+    h.bucket_smem = smem_optin - 1024;  // the bucket kernel has a little static shared memory
     Plan p;
     nn_status st = make_plan(&h, m, want, &p);
     if (st != NN_OK) return st;
@@ -327,11 +511,11 @@ nn_status nn_create(nn_handle** out) {
     }
     h->smem_optin = (size_t)optin;
     h->smem_per_sm = (size_t)per_sm;
-    h->bucket_smem = h->smem_optin;
+    h->bucket_smem = h->smem_optin - 1024;  // the bucket kernel has a little static shared memory
     if (const char* e = std::getenv("NN_SB")) h->sb_override = std::atoi(e);
     if (const char* e = std::getenv("NN_BUCKET_SMEM_KB")) {
         size_t kb = (size_t)std::atol(e);
-        if (kb >= 32 && kb * 1024 <= h->smem_optin) h->bucket_smem = kb * 1024;
+        if (kb >= 32 && kb * 1024 <= h->smem_optin - 1024) h->bucket_smem = kb * 1024;
     }
     if (set_emit_smem_all(h->smem_optin) != cudaSuccess || set_bucket_smem_all(h->smem_optin) != cudaSuccess) {
         delete h;
@@ -404,6 +588,26 @@ nn_status nn_neighbor_elements(nn_handle* h, const nn_mesh* mesh, nn_csr* out, v
 nn_status nn_neighbors_both(nn_handle* h, const nn_mesh* mesh, nn_csr* nodes, nn_csr* elems, void* ws,
                             size_t ws_bytes, int32_t* d_status, nn_stream_t stream) {
     return run(h, mesh, NN_WANT_BOTH, nodes, elems, ws, ws_bytes, d_status, reinterpret_cast<cudaStream_t>(stream));
+}
+
+nn_status nn_batch_query(nn_handle* h, const nn_batch_caps* caps, size_t* ws_bytes, size_t* staging_bytes) {
+    BatchPlan bp;
+    nn_status st = batch_plan(h, caps, &bp);
+    if (st != NN_OK) return st;
+    if (ws_bytes) *ws_bytes = bp.ws_rec;
+    if (staging_bytes) *staging_bytes = bp.table_bytes;
+    return NN_OK;
+}
+
+nn_status nn_batch_prepare(nn_handle* h, const nn_batch_caps* caps, const nn_mesh* meshes, const nn_csr* node_out,
+                           const nn_csr* elem_out, int32_t* d_status, int n_meshes, void* staging,
+                           size_t staging_bytes) {
+    return batch_prepare(h, caps, meshes, node_out, elem_out, d_status, n_meshes, staging, staging_bytes);
+}
+
+nn_status nn_batch_launch(nn_handle* h, const nn_batch_caps* caps, const void* staging, void* ws, size_t ws_bytes,
+                          nn_stream_t stream) {
+    return batch_launch(h, caps, staging, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
 }
 
 const char* nn_status_str(nn_status s) {

@@ -79,10 +79,22 @@ __device__ __forceinline__ uint32_t table_size(uint32_t c) {
     return t;
 }
 
+struct BucketOut {
+    int64_t n_nodes, first;
+    bool last;
+    int64_t* rp_n; int32_t* col_n; int64_t cap_n;
+    int64_t* rp_e; int32_t* col_e; int64_t cap_e;
+    int32_t* status;
+};
+
 template <int RB, int K>
 __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
     extern __shared__ __align__(16) uint8_t smem[];
-    const RecFmt f = p.fmt;
+    __shared__ BucketOut sh_out;
+    const bool batched = p.batch.hdr != nullptr;
+    const RecFmt f = batched ? p.batch.hdr->fmt : p.fmt;
+    const int64_t n_buckets = batched ? p.batch.hdr->n_buckets : p.n_buckets;
+    const int n_meshes = batched ? p.batch.hdr->n_meshes : 1;
     const int NB = 1 << f.sb;
     const uint32_t vmask = (uint32_t)NB - 1;
     uint64_t* cnt = reinterpret_cast<uint64_t*>(smem);  // [NB] counts / scan scratch
@@ -103,12 +115,12 @@ __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
     __syncthreads();
     for (;;) {
         const int64_t b = b_next;
-        if (b >= p.n_buckets) break;
+        if (b >= n_buckets) break;
         // take the next bucket now and start pulling its records into L2
         if (tid == 0) {
             const uint32_t nx = atomicAdd(p.ticket, 1u);
             misc[5] = nx;
-            if (nx < p.n_buckets) {
+            if (nx < n_buckets) {
                 uint64_t lo = (uint64_t)p.bstart[nx] * RB, hi = (uint64_t)p.bstart[nx + 1] * RB;
                 lo &= ~15ull;
                 hi = (hi + 15) & ~15ull;  // the record array is padded to 256 bytes
@@ -118,8 +130,29 @@ __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
                 }
             }
         }
-        const int64_t v0 = b << f.sb;
-        const int nb = (int)(p.n_nodes - v0 < (int64_t)NB ? p.n_nodes - v0 : (int64_t)NB);
+        // the mesh this bucket belongs to (the only one unless batched); its
+        // output pointers stay in shared memory until they are needed
+        if (tid == 0) {
+            BucketOut o{p.n_nodes, 0, b == n_buckets - 1, p.rp_n, p.col_n, p.cap_n, p.rp_e, p.col_e, p.cap_e, p.status};
+            if (batched) {
+                int lo = 0, hi = n_meshes;  // largest m with bucket_off[m] <= b
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (p.batch.bucket_off[mid] <= b) lo = mid;
+                    else hi = mid;
+                }
+                const BatchMesh& M = p.batch.meshes[lo];
+                o = BucketOut{M.n_nodes, p.batch.bucket_off[lo], b == p.batch.bucket_off[lo + 1] - 1, M.rp_n, M.col_n,
+                              M.cap_n, M.rp_e, M.col_e, M.cap_e, M.status};
+                if (*p.batch_err) set_status(o.status, *p.batch_err);
+            }
+            sh_out = o;
+        }
+        __syncthreads();
+        const int64_t N = sh_out.n_nodes, first = sh_out.first;
+        int32_t* const status = sh_out.status;
+        const int64_t v0 = (b - first) << f.sb;
+        const int nb = (int)(N - v0 < (int64_t)NB ? N - v0 : (int64_t)NB);
         const uint32_t r0 = p.bstart[b], r1 = p.bstart[b + 1];
 
         // counts per node: element entries (high word) and candidates (low word)
@@ -163,9 +196,9 @@ __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
         const uint64_t Tb = smem_array_excl_scan(cnt, NB, sh_scan);
         for (int l = tid; l < NB; l += BS) toff[l] = (uint32_t)cnt[l];
         const bool fast_b = Eb + Tb <= p.area_words;
-        if (want_e && tid == 0) lb_publish(p.lb_e, b, Eb);
+        if (want_e && tid == 0) lb_publish(p.lb_e, b, Eb, first);
         if (tid < 32) {  // large buckets write element lists straight to the output: need the offset now
-            const uint64_t ge = (want_e && !fast_b) ? lb_resolve(p.lb_e, b, Eb, p.status) : 0;
+            const uint64_t ge = (want_e && !fast_b) ? lb_resolve(p.lb_e, b, Eb, status, first) : 0;
             if (tid == 0) misc[1] = ge;
         }
         if (tid == 0) {
@@ -176,7 +209,7 @@ __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
                 spill_off = atomicAdd(p.spill_cursor, (unsigned long long)Tb);
                 if (spill_off + Tb > p.spill_words || Tb >= 0xFFFFFFFFull) {
                     tab_ok = false;
-                    set_status(p.status, NN_ERR_WORKSPACE);
+                    set_status(status, NN_ERR_WORKSPACE);
                 }
             }
             misc[2] = spill_off;
@@ -185,8 +218,8 @@ __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
         __syncthreads();
         uint64_t Ge = misc[1];
         const bool fast = misc[4] & 1, tab_ok = (misc[4] & 2) && want_n;
-        bool e_ok = want_e && Ge + Eb <= (uint64_t)p.cap_e;  // final for large buckets, rechecked below
-        uint32_t* elist = fast ? area : reinterpret_cast<uint32_t*>(p.col_e) + Ge;
+        bool e_ok = want_e && Ge + Eb <= (uint64_t)sh_out.cap_e;  // final for large buckets, rechecked below
+        uint32_t* elist = fast ? area : reinterpret_cast<uint32_t*>(sh_out.col_e) + Ge;
         const bool e_write = want_e && (fast || e_ok);
         uint32_t* tab = fast ? area + Eb : p.spill + misc[2];
         if (tab_ok)
@@ -215,7 +248,7 @@ __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
 #pragma unroll
                 for (int s = 0; s < K; ++s) {
                     const uint32_t y = rec_get(x, f.off_n + s * f.nb, f.nb);
-                    if (y && tab_insert(t, T - 1, shift, y - 1, p.status)) atomicAdd(&ucnt[vloc], 1u);
+                    if (y && tab_insert(t, T - 1, shift, y - 1, status)) atomicAdd(&ucnt[vloc], 1u);
                 }
             }
           }
@@ -225,7 +258,7 @@ __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
         __syncthreads();
         const uint64_t Ub = smem_array_excl_scan(cnt, NB, sh_scan);
         for (int l = tid; l < NB; l += BS) aux[l] = (uint32_t)cnt[l];
-        if (want_n && tid == 0) lb_publish(p.lb_n, b, Ub);
+        if (want_n && tid == 0) lb_publish(p.lb_n, b, Ub, first);
         uint64_t Gn = 0;
         bool n_ok = false;
         // output offsets of this bucket: resolved now for large buckets (they
@@ -233,27 +266,27 @@ __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
         // the predecessors have long published
         auto resolve = [&](bool elem_too) {
             if (tid < 32) {
-                const uint64_t gn = want_n ? lb_resolve(p.lb_n, b, Ub, p.status) : 0;
-                const uint64_t ge = (want_e && elem_too) ? lb_resolve(p.lb_e, b, Eb, p.status) : misc[1];
+                const uint64_t gn = want_n ? lb_resolve(p.lb_n, b, Ub, status, first) : 0;
+                const uint64_t ge = (want_e && elem_too) ? lb_resolve(p.lb_e, b, Eb, status, first) : misc[1];
                 if (tid == 0) {
                     misc[3] = gn;
                     misc[1] = ge;
-                    if (want_n && gn + Ub > (uint64_t)p.cap_n) set_status(p.status, NN_ERR_CAPACITY);
-                    if (want_e && ge + Eb > (uint64_t)p.cap_e) set_status(p.status, NN_ERR_CAPACITY);
+                    if (want_n && gn + Ub > (uint64_t)sh_out.cap_n) set_status(status, NN_ERR_CAPACITY);
+                    if (want_e && ge + Eb > (uint64_t)sh_out.cap_e) set_status(status, NN_ERR_CAPACITY);
                 }
             }
             __syncthreads();
             Gn = misc[3];
             Ge = misc[1];
-            n_ok = tab_ok && Gn + Ub <= (uint64_t)p.cap_n;
-            e_ok = want_e && Ge + Eb <= (uint64_t)p.cap_e;
+            n_ok = tab_ok && Gn + Ub <= (uint64_t)sh_out.cap_n;
+            e_ok = want_e && Ge + Eb <= (uint64_t)sh_out.cap_e;
             for (int l = tid; l < nb; l += BS) {
-                if (want_n) p.rp_n[v0 + l] = (int64_t)(Gn + aux[l]);
-                if (want_e) p.rp_e[v0 + l] = (int64_t)(Ge + eoff[l]);
+                if (want_n) sh_out.rp_n[v0 + l] = (int64_t)(Gn + aux[l]);
+                if (want_e) sh_out.rp_e[v0 + l] = (int64_t)(Ge + eoff[l]);
             }
-            if (b == p.n_buckets - 1 && tid == 0) {
-                if (want_n) p.rp_n[p.n_nodes] = (int64_t)(Gn + Ub);
-                if (want_e) p.rp_e[p.n_nodes] = (int64_t)(Ge + Eb);
+            if (sh_out.last && tid == 0) {
+                if (want_n) sh_out.rp_n[N] = (int64_t)(Gn + Ub);
+                if (want_e) sh_out.rp_e[N] = (int64_t)(Ge + Eb);
             }
         };
 
@@ -323,14 +356,14 @@ __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
             }
             resolve(true);
             if (n_ok)
-                for (uint64_t i = tid; i < Ub; i += BS) p.col_n[Gn + i] = (int32_t)sorted[i];
+                for (uint64_t i = tid; i < Ub; i += BS) sh_out.col_n[Gn + i] = (int32_t)sorted[i];
             if (e_ok)
-                for (uint64_t i = tid; i < Eb; i += BS) p.col_e[Ge + i] = (int32_t)sorted_e[i];
+                for (uint64_t i = tid; i < Eb; i += BS) sh_out.col_e[Ge + i] = (int32_t)sorted_e[i];
             __syncthreads();
         } else {
             // large buckets: one thread per node, rows in global memory or staged
             resolve(fast);
-            uint32_t* dst_n = stage ? stage : reinterpret_cast<uint32_t*>(p.col_n) + Gn;
+            uint32_t* dst_n = stage ? stage : reinterpret_cast<uint32_t*>(sh_out.col_n) + Gn;
             int has_long = 0;
             if (n_ok) {
                 for (int l = tid; l < NB; l += BS) {
@@ -365,9 +398,9 @@ __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
             }
             __syncthreads();
             if (stage && n_ok)
-                for (uint64_t i = tid; i < Ub; i += BS) p.col_n[Gn + i] = (int32_t)stage[i];
+                for (uint64_t i = tid; i < Ub; i += BS) sh_out.col_n[Gn + i] = (int32_t)stage[i];
             if (fast && e_ok)
-                for (uint64_t i = tid; i < Eb; i += BS) p.col_e[Ge + i] = (int32_t)elist[i];
+                for (uint64_t i = tid; i < Eb; i += BS) sh_out.col_e[Ge + i] = (int32_t)elist[i];
             __syncthreads();
         }
         b_next = (int64_t)misc[5];
@@ -375,9 +408,15 @@ __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
     }
 }
 
+// Allow up to `bytes` of dynamic shared memory, less the kernel's own static
+// shared memory (the sum may not exceed the per-block opt-in limit).
 template <int RB, int K>
 cudaError_t set_attr(size_t bytes) {
-    return cudaFuncSetAttribute(k_bucket<RB, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k_bucket<RB, K>);
+    if (e != cudaSuccess) return e;
+    const size_t dyn = bytes > a.sharedSizeBytes ? bytes - a.sharedSizeBytes : 0;
+    return cudaFuncSetAttribute(k_bucket<RB, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
 }
 
 }  // namespace

@@ -78,19 +78,22 @@ __device__ inline uint64_t lookback(uint64_t* state, uint64_t t, uint64_t agg, i
 // a time, consuming the ready ones nearest to t and stopping at the first
 // inclusive prefix, then publishes t's inclusive prefix.  Only the nearest
 // not-yet-ready predecessor is ever waited for.
-__device__ __forceinline__ void lb_publish(uint64_t* state, uint64_t t, uint64_t agg) {
-    st_release(&state[t], (t == 0 ? LB_INC : LB_AGG) | agg);
+// `first` is the first tile of t's chain (a batch restarts the scan at every
+// mesh): tiles before it count as an inclusive zero.
+__device__ __forceinline__ void lb_publish(uint64_t* state, uint64_t t, uint64_t agg, uint64_t first = 0) {
+    st_release(&state[t], (t == first ? LB_INC : LB_AGG) | agg);
 }
 
-__device__ inline uint64_t lb_resolve(uint64_t* state, uint64_t t, uint64_t agg, int32_t* status) {
+__device__ inline uint64_t lb_resolve(uint64_t* state, uint64_t t, uint64_t agg, int32_t* status,
+                                      uint64_t first = 0) {
     const int lane = threadIdx.x & 31;
-    if (t == 0) return 0;
+    if (t == first) return 0;
     uint64_t excl = 0;
     int64_t p = (int64_t)t - 1;
     uint64_t t0 = 0;
     for (;;) {
         const int64_t idx = p - lane;
-        const uint64_t s = idx >= 0 ? ld_acquire(&state[idx]) : LB_INC;  // before tile 0: inclusive zero
+        const uint64_t s = idx >= (int64_t)first ? ld_acquire(&state[idx]) : LB_INC;  // before the chain: zero
         const unsigned not_ready = __ballot_sync(0xffffffffu, (s >> 62) == 0);
         const int k = not_ready ? __ffs(not_ready) - 1 : 32;  // lanes 0..k-1 are ready
         const unsigned ready_mask = k == 32 ? 0xffffffffu : ((1u << k) - 1);

@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(OFFSETS_THREADS) k_offsets(OffsetsParams p) {
     if (threadIdx.x == 0) sh_tile = atomicAdd(p.ticket, 1u);
     __syncthreads();
     const uint32_t tile = sh_tile;
-    const int64_t B = p.n_buckets;
+    const int64_t B = p.hdr ? p.hdr->n_buckets : p.n_buckets;
     const int64_t b = (int64_t)tile * blockDim.x + threadIdx.x;
     uint64_t tot = 0;
     if (b < B)

@@ -46,6 +46,8 @@ struct EmitParams {
     int32_t* status;
 };
 
+struct BatchHeader;
+
 struct OffsetsParams {
     uint32_t* hist;
     int n_cta;
@@ -56,6 +58,40 @@ struct OffsetsParams {
     uint32_t* ticket;
     uint64_t rec_cap;       // bucket starts are clamped to the record array
     int32_t* status;
+    const BatchHeader* hdr; // batches: the bucket count comes from the header
+};
+
+// ------------------------------------------------------------------ batches
+// A batch is the disjoint union of many meshes built by one launch sequence.
+// Its description lives in device memory (copied from host staging by the
+// launch), so the same captured sequence serves any batch that fits the
+// workspace capacity: header, then one BatchMesh per mesh, then the element
+// and bucket offsets of the meshes (n_meshes + 1 each).
+struct BatchMesh {
+    int32_t type;
+    int32_t k;
+    int64_t n_nodes, n_elems, n_conn;
+    const int32_t* conn;
+    const int64_t* elem_ptr;
+    const uint8_t* elem_type;
+    int64_t* rp_n; int32_t* col_n; int64_t cap_n;
+    int64_t* rp_e; int32_t* col_e; int64_t cap_e;
+    int32_t* status;
+};
+
+struct BatchHeader {
+    RecFmt fmt;
+    int32_t n_meshes;
+    int64_t n_elems;    // elements of all meshes
+    int64_t n_buckets;  // buckets of all meshes (each mesh starts a new bucket)
+    int64_t n_records;  // record capacity (incidences of all meshes)
+};
+
+struct BatchTables {
+    const BatchHeader* hdr;
+    const BatchMesh* meshes;
+    const int64_t* elem_off;    // [n_meshes+1]
+    const int64_t* bucket_off;  // [n_meshes+1]
 };
 
 // Bucket pass: one CTA per bucket (persistent, buckets taken in order),
@@ -76,6 +112,8 @@ struct BucketParams {
     int64_t* rp_e; int32_t* col_e; int64_t cap_e;
     int32_t* status;
     uint32_t area_words;    // shared-memory words available for tables and lists
+    BatchTables batch;      // batch.hdr != nullptr: format, bucket count and meshes come from the tables
+    const int32_t* batch_err;  // batches: status of the shared offsets scan, copied to every mesh
 };
 
 constexpr int EMIT_THREADS = 1024;
@@ -87,6 +125,10 @@ cudaError_t launch_hist(const EmitParams& p, size_t smem, cudaStream_t s);
 cudaError_t launch_part(const EmitParams& p, cudaStream_t s);
 cudaError_t launch_offsets(const OffsetsParams& p, cudaStream_t s);
 cudaError_t launch_bucket(const BucketParams& p, int grid, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_batch_emit(const BatchTables& bt, uint32_t* bcount, uint32_t* gcur, uint8_t* rec,
+                              uint64_t* lb_off, uint64_t* lb_n, uint64_t* lb_e, uint32_t* ctrl, int grid,
+                              int stage, cudaStream_t s);
+int batch_threads();
 cudaError_t set_emit_smem_all(size_t bytes);
 cudaError_t set_bucket_smem_all(size_t bytes);
 nn_status build_with_limits(int sms, size_t smem_optin, size_t smem_per_sm, const nn_mesh* m, int want,

@@ -40,6 +40,11 @@ class NNCSR(C.Structure):
     _fields_ = [("row_ptr", C.c_void_p), ("col", C.c_void_p), ("col_capacity", C.c_int64)]
 
 
+class NNBatchCaps(C.Structure):
+    _fields_ = [("max_meshes", C.c_int32), ("want", C.c_int32), ("max_elems", C.c_int64),
+                ("max_nodes", C.c_int64), ("max_conn", C.c_int64), ("sb", C.c_int32)]
+
+
 class NNError(RuntimeError):
     def __init__(self, code: int, where: str = ""):
         self.code = code
@@ -81,6 +86,12 @@ def lib():
             L.nn_plan_info.restype = C.c_int
             L.nn_neighbors_both_noalloc.argtypes = [C.POINTER(NNMesh), C.POINTER(NNCSR), C.POINTER(NNCSR), P, P]
             L.nn_neighbors_both_noalloc.restype = C.c_int
+            L.nn_batch_query.argtypes = [P, C.POINTER(NNBatchCaps), C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
+            L.nn_batch_query.restype = C.c_int
+            L.nn_batch_prepare.argtypes = [P, C.POINTER(NNBatchCaps), P, P, P, P, C.c_int, P, C.c_size_t]
+            L.nn_batch_prepare.restype = C.c_int
+            L.nn_batch_launch.argtypes = [P, C.POINTER(NNBatchCaps), P, P, C.c_size_t, P]
+            L.nn_batch_launch.restype = C.c_int
             L.nn_status_str.argtypes = [C.c_int]
             L.nn_status_str.restype = C.c_char_p
             _lib = L
@@ -142,6 +153,28 @@ NOALLOC_SCRATCH_BYTES = 32 << 20
 def nn_neighbors_both_noalloc(mesh: NNMesh, nodes: NNCSR, elems: NNCSR, d_status: int, stream: int) -> int:
     """Both CSRs with the library's fixed device scratch instead of a workspace (allocates nothing)."""
     return lib().nn_neighbors_both_noalloc(C.byref(mesh), C.byref(nodes), C.byref(elems), d_status, stream)
+
+
+def nn_batch_query(h: int, caps: NNBatchCaps):
+    ws = C.c_size_t()
+    sg = C.c_size_t()
+    st = lib().nn_batch_query(h, C.byref(caps), C.byref(ws), C.byref(sg))
+    if st:
+        raise NNError(st, "nn_batch_query")
+    return ws.value, sg.value
+
+
+def nn_batch_prepare(h: int, caps: NNBatchCaps, meshes, node_out, elem_out, d_status: int, n: int,
+                     staging: int, staging_bytes: int) -> int:
+    """meshes / node_out / elem_out: ctypes arrays of NNMesh / NNCSR (or None)."""
+    return lib().nn_batch_prepare(h, C.byref(caps), C.cast(meshes, C.c_void_p) if meshes is not None else None,
+                                  C.cast(node_out, C.c_void_p) if node_out is not None else None,
+                                  C.cast(elem_out, C.c_void_p) if elem_out is not None else None,
+                                  d_status, n, staging, staging_bytes)
+
+
+def nn_batch_launch(h: int, caps: NNBatchCaps, staging: int, ws: int, ws_bytes: int, stream: int) -> int:
+    return lib().nn_batch_launch(h, C.byref(caps), staging, ws, ws_bytes, stream)
 
 
 STAGES = ("init", "hist", "offsets", "part", "bucket")
@@ -287,4 +320,81 @@ class Builder:
         for k, (rp, col) in out.items():
             nnz = int(rp[-1].item()) if res["status"] == 0 else col.numel()
             res[k] = (rp, col[:nnz])
+        return res
+
+
+class BatchBuilder:
+    """Batched builds: one launch sequence for many meshes (capacity fixed at creation).
+
+    ``prepare`` writes a batch into pinned host staging (host only); ``launch``
+    enqueues it.  ``launch`` may be captured once in a CUDA graph and the graph
+    replayed after each ``prepare``."""
+
+    def __init__(self, max_meshes: int, max_elems: int, max_nodes: int, max_conn: int, want: int = WANT_BOTH,
+                 sb: int = 0, device=None, handle=None, extra_ws: int = 0):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.own = handle is None
+        with torch.cuda.device(self.device):
+            self.h = handle if handle is not None else nn_create()
+        self.caps = NNBatchCaps(max_meshes, want, max_elems, max_nodes, max_conn, sb)
+        self.ws_bytes, self.staging_bytes = nn_batch_query(self.h, self.caps)
+        self.ws_bytes += extra_ws
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        self.staging = torch.empty(self.staging_bytes, dtype=torch.uint8, pin_memory=True)
+        self.status = torch.zeros(max_meshes, dtype=torch.int32, device=self.device)
+        self.want = want
+
+    def close(self):
+        if self.own and self.h:
+            nn_destroy(self.h)
+        self.h = None
+
+    def alloc_outputs(self, dm: DeviceMesh):
+        torch = self.torch
+        nc = (2 if dm.etype in (TRI, QUAD) else 3) * dm.n_conn
+        out = {}
+        if self.want & WANT_NODES:
+            out["nodes"] = (torch.empty(dm.n_nodes + 1, dtype=torch.int64, device=self.device),
+                            torch.empty(max(nc, 1), dtype=torch.int32, device=self.device))
+        if self.want & WANT_ELEMS:
+            out["elems"] = (torch.empty(dm.n_nodes + 1, dtype=torch.int64, device=self.device),
+                            torch.empty(max(dm.n_conn, 1), dtype=torch.int32, device=self.device))
+        return out
+
+    def prepare(self, dmeshes, outs) -> int:
+        n = len(dmeshes)
+        M = (NNMesh * max(n, 1))(*[d.struct() for d in dmeshes])
+
+        def csrs(key):
+            if not (self.want & (WANT_NODES if key == "nodes" else WANT_ELEMS)):
+                return None
+            return (NNCSR * max(n, 1))(*[NNCSR(o[key][0].data_ptr(), o[key][1].data_ptr(), o[key][1].numel())
+                                          for o in outs])
+        self._keep = (M, csrs("nodes"), csrs("elems"))
+        return nn_batch_prepare(self.h, self.caps, M, self._keep[1], self._keep[2], self.status.data_ptr(), n,
+                                self.staging.data_ptr(), self.staging_bytes)
+
+    def launch(self, stream=None) -> int:
+        s = (stream or self.torch.cuda.current_stream(self.device)).cuda_stream
+        return nn_batch_launch(self.h, self.caps, self.staging.data_ptr(), self.ws.data_ptr(), self.ws_bytes, s)
+
+    def run(self, dmeshes):
+        """Build a batch, wait, and return per-mesh results (col trimmed) and statuses."""
+        outs = [self.alloc_outputs(d) for d in dmeshes]
+        st = self.prepare(dmeshes, outs)
+        if st:
+            raise NNError(st, "nn_batch_prepare")
+        st = self.launch()
+        if st:
+            raise NNError(st, "nn_batch_launch")
+        self.torch.cuda.synchronize(self.device)
+        stat = self.status[: len(dmeshes)].cpu().tolist()
+        res = []
+        for o, s_ in zip(outs, stat):
+            r = {"status": int(s_)}
+            for k, (rp, col) in o.items():
+                r[k] = (rp, col[: int(rp[-1].item())] if s_ == 0 else col)
+            res.append(r)
         return res
