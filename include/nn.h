@@ -163,6 +163,17 @@ nn_status nn_batch_prepare(nn_handle* h, const nn_batch_caps* caps, const nn_mes
 nn_status nn_batch_launch(nn_handle* h, const nn_batch_caps* caps, const void* staging, void* ws,
                           size_t ws_bytes, nn_stream_t stream);
 
+/* Seeded synthetic grid meshes generated on the device -- input generation
+ * for benchmarks and the serving loop, not part of the method.  The result is
+ * identical to the host generator (paper_1604_04689_gb300/meshgen.py):
+ * n x n (tri/quad) or n x n x n (tet/hex) nodes, triangles split along a
+ * seeded diagonal per quad, cube cells split into 6 Kuhn tetrahedra, node ids
+ * (permute_nodes) and element order (permute_elems) relabelled by seeded
+ * bijections.  With conn == NULL only *n_nodes and *n_elems are returned. */
+nn_status nn_generate_grid(int32_t type, int64_t n, uint64_t seed, int permute_nodes, int permute_elems,
+                           int32_t* conn, int64_t conn_capacity, int64_t* n_nodes, int64_t* n_elems,
+                           nn_stream_t stream);
+
 /* Per-stage device timing (used by the benchmark).  While enabled, compute
  * calls record CUDA events on their stream between their stages:
  *   0 workspace/status init, 1 bucket histogram, 2 bucket offsets,

@@ -92,6 +92,9 @@ def lib():
             L.nn_batch_prepare.restype = C.c_int
             L.nn_batch_launch.argtypes = [P, C.POINTER(NNBatchCaps), P, P, C.c_size_t, P]
             L.nn_batch_launch.restype = C.c_int
+            L.nn_generate_grid.argtypes = [C.c_int32, C.c_int64, C.c_uint64, C.c_int, C.c_int, P, C.c_int64,
+                                           C.POINTER(C.c_int64), C.POINTER(C.c_int64), P]
+            L.nn_generate_grid.restype = C.c_int
             L.nn_status_str.argtypes = [C.c_int]
             L.nn_status_str.restype = C.c_char_p
             _lib = L
@@ -175,6 +178,35 @@ def nn_batch_prepare(h: int, caps: NNBatchCaps, meshes, node_out, elem_out, d_st
 
 def nn_batch_launch(h: int, caps: NNBatchCaps, staging: int, ws: int, ws_bytes: int, stream: int) -> int:
     return lib().nn_batch_launch(h, C.byref(caps), staging, ws, ws_bytes, stream)
+
+
+def nn_generate_grid(etype: int, n: int, seed: int, permute_nodes: bool, permute_elems: bool, conn: int,
+                     capacity: int, stream: int):
+    """Generate a seeded grid mesh into device memory; returns (status, n_nodes, n_elems)."""
+    nn_ = C.c_int64()
+    ne = C.c_int64()
+    st = lib().nn_generate_grid(etype, n, seed & ((1 << 64) - 1), int(permute_nodes), int(permute_elems), conn,
+                                capacity, C.byref(nn_), C.byref(ne), stream)
+    return st, nn_.value, ne.value
+
+
+def generate_grid(etype: int, n: int, seed: int, permute_nodes: bool = True, permute_elems=None, device=None,
+                  stream=None) -> "DeviceMesh":
+    """A DeviceMesh generated on the device (same mesh as meshgen's tri/quad/tet/hex_grid)."""
+    import torch
+    if permute_elems is None:
+        permute_elems = etype != HEX            # meshgen's defaults
+    st, N, T = nn_generate_grid(etype, n, seed, permute_nodes, permute_elems, None, 0, 0)
+    if st:
+        raise NNError(st, "nn_generate_grid")
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    conn = torch.empty(T * NPE[etype], dtype=torch.int32, device=dev)
+    s = (stream or torch.cuda.current_stream(dev)).cuda_stream
+    st, _, _ = nn_generate_grid(etype, n, seed, permute_nodes, permute_elems, conn.data_ptr() if T else None,
+                                conn.numel(), s)
+    if st:
+        raise NNError(st, "nn_generate_grid")
+    return DeviceMesh(etype, N, conn)
 
 
 STAGES = ("init", "hist", "offsets", "part", "bucket")
@@ -287,8 +319,9 @@ class Builder:
                                         device=self.device))
         return out
 
-    def launch(self, dm: DeviceMesh, want: int, out: dict, ws=None, ws_bytes=None, stream=None) -> int:
-        """Enqueue one build (no sync).  Returns the host status code."""
+    def launch(self, dm: DeviceMesh, want: int, out: dict, ws=None, ws_bytes=None, stream=None, status=None) -> int:
+        """Enqueue one build (no sync).  Returns the host status code.  ``status``: a device int32
+        tensor to receive the device status instead of the builder's own."""
         torch = self.torch
         if ws is None:
             nbytes, _, _ = self.query(dm, want)
@@ -300,14 +333,12 @@ class Builder:
         def csr(pair):
             rp, col = pair
             return NNCSR(rp.data_ptr(), col.data_ptr(), col.numel())
+        sp = (status if status is not None else self.status).data_ptr()
         if want == WANT_NODES:
-            return nn_neighbor_nodes(self.h, mesh, csr(out["nodes"]), ws.data_ptr(), ws_bytes,
-                                     self.status.data_ptr(), s)
+            return nn_neighbor_nodes(self.h, mesh, csr(out["nodes"]), ws.data_ptr(), ws_bytes, sp, s)
         if want == WANT_ELEMS:
-            return nn_neighbor_elements(self.h, mesh, csr(out["elems"]), ws.data_ptr(), ws_bytes,
-                                        self.status.data_ptr(), s)
-        return nn_neighbors_both(self.h, mesh, csr(out["nodes"]), csr(out["elems"]), ws.data_ptr(), ws_bytes,
-                                 self.status.data_ptr(), s)
+            return nn_neighbor_elements(self.h, mesh, csr(out["elems"]), ws.data_ptr(), ws_bytes, sp, s)
+        return nn_neighbors_both(self.h, mesh, csr(out["nodes"]), csr(out["elems"]), ws.data_ptr(), ws_bytes, sp, s)
 
     def build(self, dm: DeviceMesh, want: int = WANT_BOTH):
         """Build and return {'status': int, 'nodes': (row_ptr, col), 'elems': (row_ptr, col)} (col trimmed)."""
