@@ -22,6 +22,7 @@ struct nn_handle {
     size_t bucket_smem = 0;    // largest dynamic shared memory of the bucket kernel
     size_t smem_per_sm = 0;
     int sb_override = -1;      // fixed bucket width (tests / tuning), -1 = automatic
+    int part_mode = -1;        // -1 automatic, 0 one scattered store per record (tests)
     // per-stage timing (nn_profile_*)
     bool prof = false;
     bool pending = false;
@@ -54,8 +55,9 @@ struct Plan {
     int64_t B = 0;
     int G = 1;
     int G_part = 1;
+    int G_fine = 1;
     size_t emit_smem = 0;
-    size_t off_hist = 0, off_bstart = 0, off_gcur = 0, off_rec = 0, off_lb_off = 0, off_lb_n = 0, off_lb_e = 0,
+    size_t off_hist = 0, off_bstart = 0, off_gcur = 0, off_gcur_c = 0, off_rec_tmp = 0, off_rec = 0, off_lb_off = 0, off_lb_n = 0, off_lb_e = 0,
            off_ctrl = 0, off_spill = 0, zero_begin = 0, zero_end = 0;
     size_t ws_min = 0, ws_rec = 0;
     int bucket_grid = 0;
@@ -103,7 +105,7 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     // prefer a shared-memory size that lets two bucket CTAs share an SM, so one
     // CTA's barriers and lookback waits overlap the other's memory traffic
     int sb = -1;
-    size_t bsmem = std::min(h->bucket_smem, h->smem_per_sm / 2 - 1024);
+    size_t bsmem = std::min(h->bucket_smem, h->smem_per_sm / 2 - 2048);
     for (int pass = 0; pass < 2 && sb < 0; ++pass) {
         if (pass == 1) bsmem = h->bucket_smem;
         for (int s = SB_MAX; s >= SB_MIN + 2; --s) {
@@ -141,6 +143,16 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     f.off_n = (want & NN_WANT_ELEMS) ? sb + 1 + f.eb : sb;
     int total = (want & NN_WANT_NODES) ? f.off_n + p.k * f.nb : sb + 1 + f.eb;
     if (total > 128) return NN_ERR_ARG;
+    // partition: tile-sorted (one pass for <= 256 buckets, else coarse + fine
+    // with the fine digit kept in the record) unless that field does not fit
+    int cs = 0;
+    while (((p.B + (1ll << cs) - 1) >> cs) > 256) ++cs;
+    f.cshift = -1;
+    f.off_fb = total;
+    if (h->part_mode != 0 && total + cs <= 128) {
+        f.cshift = cs;
+        total += cs;
+    }
     f.rb = total <= 64 ? 8 : 16;
 
     // element-walk CTAs: one or two per SM, each a fixed slice of elements
@@ -150,12 +162,17 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     const int cps = p.emit_smem + 2048 <= 113 * 1024 ? 2 : 1;
     p.G = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sms * cps, (n_units + 2047) / 2048));
     p.G_part = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sms * 2, (n_units + 511) / 512));
+    if (f.cshift >= 0)  // tile-sorted passes: 256-thread CTAs, several per SM
+        p.G_part = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sms * 4, (n_units + 511) / 512));
+    p.G_fine = h->sms * 4;
 
     // workspace layout
     size_t o = 0;
     p.off_hist = o; o = align_up(o + (size_t)p.G * p.B * 4);
     p.off_bstart = o; o = align_up(o + ((size_t)p.B + 1) * 4);
     p.off_gcur = o; o = align_up(o + (size_t)p.B * 4);
+    p.off_gcur_c = o; o = align_up(o + 256 * 4);
+    p.off_rec_tmp = o; o = align_up(o + (f.cshift > 0 ? (size_t)p.n_conn * f.rb : 0));
     p.off_rec = o; o = align_up(o + (size_t)p.n_conn * f.rb);
     p.zero_begin = o;
     p.off_lb_off = o; o = align_up(o + (size_t)((p.B + OFFSETS_THREADS - 1) / OFFSETS_THREADS) * 8 + 8);
@@ -233,6 +250,8 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
     ep.n_cta_part = p.G_part;
     ep.hist = reinterpret_cast<uint32_t*>(w + p.off_hist);
     ep.gcur = reinterpret_cast<uint32_t*>(w + p.off_gcur);
+    ep.gcur_coarse = reinterpret_cast<uint32_t*>(w + p.off_gcur_c);
+    ep.rec_tmp = w + p.off_rec_tmp;
     ep.rec = w + p.off_rec;
     ep.rec_cap = (uint64_t)p.n_conn;
     ep.status = d_status;
@@ -243,6 +262,8 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
     op.n_buckets = p.B;
     op.bstart = reinterpret_cast<uint32_t*>(w + p.off_bstart);
     op.gcur = ep.gcur;
+    op.gcur_coarse = ep.gcur_coarse;
+    op.cshift = p.fmt.cshift;
     op.lb_state = reinterpret_cast<uint64_t*>(w + p.off_lb_off);
     op.ticket = ctrl + 0;
     op.rec_cap = (uint64_t)p.n_conn;
@@ -278,7 +299,11 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
     prof_mark(h, 2, s);
     if (launch_offsets(op, s) != cudaSuccess) return NN_ERR_CUDA;
     prof_mark(h, 3, s);
-    if (launch_part(ep, s) != cudaSuccess) return NN_ERR_CUDA;
+    if (p.fmt.cshift >= 0) {
+        if (launch_part_sorted(ep, op.bstart, p.G_fine, s) != cudaSuccess) return NN_ERR_CUDA;
+    } else if (launch_part(ep, s) != cudaSuccess) {
+        return NN_ERR_CUDA;
+    }
     prof_mark(h, 4, s);
     if (launch_bucket(bp, p.bucket_grid, bucket_threads(), p.bucket_smem, s) != cudaSuccess)
         return NN_ERR_CUDA;
@@ -330,7 +355,7 @@ nn_status batch_plan(const nn_handle* h, const nn_batch_caps* c, BatchPlan* out)
     p.ws_rec = o + (((size_t)16 << 20) + (size_t)c->max_conn * 8);
     // shared memory: two CTAs per SM for narrow buckets, else one
     const size_t fixed = BUCKET_FIXED_PER_NODE * ((size_t)1 << p.sb) + BUCKET_FIXED;
-    p.bucket_smem = p.sb <= 7 ? std::min(h->bucket_smem, h->smem_per_sm / 2 - 1024) : h->bucket_smem;
+    p.bucket_smem = p.sb <= 7 ? std::min(h->bucket_smem, h->smem_per_sm / 2 - 2048) : h->bucket_smem;
     if (fixed + 4096 * 4 > p.bucket_smem) p.bucket_smem = h->bucket_smem;
     if (fixed + 4096 * 4 > p.bucket_smem) return NN_ERR_ARG;
     p.area_words = (uint32_t)((p.bucket_smem - fixed) / 4);
@@ -405,6 +430,8 @@ nn_status batch_prepare(nn_handle* h, const nn_batch_caps* c, const nn_mesh* mes
     const int total = (c->want & NN_WANT_NODES) ? f.off_n + 3 * f.nb : f.sb + 1 + f.eb;
     if (total > 128) return NN_ERR_ARG;
     f.rb = 16;
+    f.cshift = -1;
+    f.off_fb = total;
     hdr->fmt = f;
     hdr->n_meshes = n;
     hdr->n_elems = E;
@@ -513,6 +540,7 @@ nn_status nn_create(nn_handle** out) {
     h->smem_per_sm = (size_t)per_sm;
     h->bucket_smem = h->smem_optin - 1024;  // the bucket kernel has a little static shared memory
     if (const char* e = std::getenv("NN_SB")) h->sb_override = std::atoi(e);
+    if (const char* e = std::getenv("NN_PART")) h->part_mode = std::strcmp(e, "scatter") == 0 ? 0 : -1;
     if (const char* e = std::getenv("NN_BUCKET_SMEM_KB")) {
         size_t kb = (size_t)std::atol(e);
         if (kb >= 32 && kb * 1024 <= h->smem_optin - 1024) h->bucket_smem = kb * 1024;

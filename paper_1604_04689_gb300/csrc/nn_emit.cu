@@ -255,6 +255,239 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_part(EmitParams p) {
     }
 }
 
+// ------------------------------------------------ tile-sorted partition
+// A CTA builds the records of a tile of work units, ranks them by radix digit
+// in shared memory, reserves one global range per digit present in the tile
+// (one atomic per digit, not per record) and writes each digit's run
+// contiguously, so global stores are coalesced runs instead of one scattered
+// 16-byte store per record.
+
+// Exclusive scan of hist[0..n) (n <= blockDim.x) into dof; returns the total.
+// Ends with a barrier: every thread may read any dof entry afterwards.
+__device__ __forceinline__ uint32_t tile_scan(const uint32_t* hist, uint32_t* dof, int n, uint64_t* sh) {
+    const uint64_t x = threadIdx.x < n ? hist[threadIdx.x] : 0;
+    uint64_t total;
+    const uint64_t ex = block_excl_scan(x, &total, sh);
+    if (threadIdx.x < n) dof[threadIdx.x] = (uint32_t)ex;
+    __syncthreads();
+    return (uint32_t)total;
+}
+
+template <int TYPE>
+struct SortShape {
+    static constexpr int UNIT = TYPE == NN_TRI ? 4 : 1;
+    static constexpr int NPE = TYPE == NN_MIXED ? 8 : ElemT<(TYPE == NN_MIXED ? NN_HEX : TYPE)>::NPE;
+    static constexpr int UPT = (TYPE == NN_TET || TYPE == NN_QUAD) ? 2 : 1;
+    static constexpr int NI = NPE * UNIT;
+    static constexpr int RPT = NI * UPT;
+    static constexpr int TILE = SORT_THREADS * RPT;
+};
+
+template <int TYPE>
+__host__ __device__ constexpr size_t coarse_smem() {
+    return (size_t)SortShape<TYPE>::TILE * 17 + 3 * 256 * 4;
+}
+constexpr int FINE_RPT = 4;
+constexpr int FINE_TILE = SORT_THREADS * FINE_RPT;
+constexpr size_t FINE_SMEM = (size_t)FINE_TILE * 17 + 3 * 256 * 4 + 257 * 4;
+
+template <int TYPE>
+__device__ __forceinline__ Rec make_rec(const RecFmt& f, const int32_t* e_nd, int i, int t, int64_t e) {
+    constexpr int NPE = SortShape<TYPE>::NPE;
+    const int32_t v = e_nd[i];
+    int nf = 0;
+#pragma unroll
+    for (int q = 0; q < NPE; ++q) nf |= (q < i) && (e_nd[q] == v);
+    const int K = TYPE == NN_MIXED ? k_of(t) : ElemT<(TYPE == NN_MIXED ? NN_HEX : TYPE)>::K;
+    Rec r{(uint64_t)((uint32_t)v & ((1u << f.sb) - 1)), 0};
+    if (f.want & NN_WANT_ELEMS) {
+        rec_put(r, (uint64_t)nf, f.off_nf);
+        rec_put(r, (uint64_t)e, f.off_e);
+    }
+    if (f.want & NN_WANT_NODES) {
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            if (s >= K) break;
+            const int li = TYPE == NN_MIXED ? nbr_of(t, i, s) : ElemT<(TYPE == NN_MIXED ? NN_HEX : TYPE)>::nbr(i, s);
+            const int32_t y = e_nd[li];
+            rec_put(r, y == v ? 0ull : (uint64_t)(uint32_t)(y + 1), f.off_n + s * f.nb);
+        }
+    }
+    if (f.cshift > 0) rec_put(r, (uint64_t)(((uint32_t)v >> f.sb) & ((1u << f.cshift) - 1)), f.off_fb);
+    return r;
+}
+
+template <int RB>
+__device__ __forceinline__ void store_rec(uint8_t* base, uint64_t pos, const ulonglong2& r) {
+    if constexpr (RB == 8) reinterpret_cast<uint64_t*>(base)[pos] = r.x;
+    else reinterpret_cast<ulonglong2*>(base)[pos] = r;
+}
+template <int RB>
+__device__ __forceinline__ ulonglong2 load_rec2(const uint8_t* base, uint64_t pos) {
+    if constexpr (RB == 8) return make_ulonglong2(__ldg(reinterpret_cast<const unsigned long long*>(base) + pos), 0);
+    else return __ldg(reinterpret_cast<const ulonglong2*>(base) + pos);
+}
+
+// First (or only) pass: records from the connectivity, radix digit = coarse
+// region (two levels) or bucket (one level, at most 256 buckets).
+template <int TYPE, int RB>
+__global__ void __launch_bounds__(SORT_THREADS) k_part_coarse(EmitParams p) {
+    using S = SortShape<TYPE>;
+    constexpr int UNIT = S::UNIT, NPE = S::NPE, UPT = S::UPT, NI = S::NI, TILE = S::TILE;
+    extern __shared__ __align__(16) uint8_t sm[];
+    ulonglong2* out = reinterpret_cast<ulonglong2*>(sm);
+    uint8_t* odig = reinterpret_cast<uint8_t*>(out + TILE);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(odig + TILE);
+    uint32_t* dof = hist + 256;
+    uint32_t* gbase = dof + 256;
+    __shared__ uint64_t sh_scan[34];
+    const RecFmt f = p.fmt;
+    const bool two = f.cshift > 0;
+    const int dshift = f.sb + (two ? f.cshift : 0);
+    uint32_t* cursor = two ? p.gcur_coarse : p.gcur;
+    uint8_t* dst = two ? p.rec_tmp : p.rec;
+    const int64_t n_units = (p.n_elems + UNIT - 1) / UNIT;
+    const int64_t u0 = n_units * blockIdx.x / gridDim.x, u1 = n_units * (blockIdx.x + 1) / gridDim.x;
+    for (int64_t tu = u0; tu < u1; tu += (int64_t)SORT_THREADS * UPT) {
+        hist[threadIdx.x] = 0;
+        __syncthreads();
+        int32_t nd[UPT][NI];
+        bool ok[UPT][UNIT];
+        int t[UPT];
+        uint16_t rk[UPT][NI];
+        uint8_t dg[UPT][NI];
+#pragma unroll
+        for (int k = 0; k < UPT; ++k) {
+            const int64_t u = tu + (int64_t)threadIdx.x * UPT + k;
+#pragma unroll
+            for (int w = 0; w < UNIT; ++w) ok[k][w] = false;
+            t[k] = TYPE == NN_MIXED ? NN_HEX : TYPE;
+            if (u < u1) t[k] = load_unit<TYPE>(p, u, nd[k], ok[k]);
+            const int npe = TYPE == NN_MIXED ? npe_of(t[k]) : NPE;
+#pragma unroll
+            for (int j = 0; j < NI; ++j) {
+                const int w = j / NPE, i = j % NPE;
+                dg[k][j] = 0;
+                rk[k][j] = 0xFFFF;
+                if (ok[k][w] && i < npe) {
+                    const uint32_t d = (uint32_t)nd[k][j] >> dshift;
+                    dg[k][j] = (uint8_t)d;
+                    rk[k][j] = (uint16_t)atomicAdd(&hist[d], 1u);
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t n_tile = tile_scan(hist, dof, 256, sh_scan);
+        if (hist[threadIdx.x]) gbase[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], hist[threadIdx.x]);
+#pragma unroll
+        for (int k = 0; k < UPT; ++k) {
+            const int64_t u = tu + (int64_t)threadIdx.x * UPT + k;
+#pragma unroll
+            for (int j = 0; j < NI; ++j) {
+                if (rk[k][j] == 0xFFFF) continue;
+                const int w = j / NPE, i = j % NPE;
+                const Rec r = make_rec<TYPE>(f, nd[k] + w * NPE, i, t[k], u * UNIT + w);
+                const uint32_t q = dof[dg[k][j]] + rk[k][j];
+                out[q] = make_ulonglong2(r.lo, r.hi);
+                odig[q] = dg[k][j];
+            }
+        }
+        __syncthreads();
+        for (uint32_t q = threadIdx.x; q < n_tile; q += SORT_THREADS) {
+            const uint32_t d = odig[q];
+            const uint64_t pos = (uint64_t)gbase[d] + (q - dof[d]);
+            if (pos < p.rec_cap) store_rec<RB>(dst, pos, out[q]);
+        }
+        __syncthreads();
+    }
+}
+
+// Second pass: one coarse region per work item group; radix digit = bucket
+// inside the region (stored in the record by the first pass).
+template <int RB>
+__global__ void __launch_bounds__(SORT_THREADS) k_part_fine(EmitParams p, const uint32_t* bstart) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    ulonglong2* out = reinterpret_cast<ulonglong2*>(sm);
+    uint8_t* odig = reinterpret_cast<uint8_t*>(out + FINE_TILE);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(odig + FINE_TILE);
+    uint32_t* dof = hist + 256;
+    uint32_t* gbase = dof + 256;
+    uint32_t* tpre = gbase + 256;  // [257] first tile of each coarse region
+    __shared__ uint64_t sh_scan[34];
+    const RecFmt f = p.fmt;
+    const int cs = f.cshift;
+    const int64_t B = p.n_buckets;
+    const int R1 = (int)((B + (1ll << cs) - 1) >> cs);
+    const int d0 = threadIdx.x;
+    uint32_t my_tiles = 0;
+    if (d0 < R1) {
+        const uint32_t a = bstart[(int64_t)d0 << cs];
+        const int64_t e_ = ((int64_t)d0 + 1) << cs;
+        const uint32_t b = bstart[e_ < B ? e_ : B];
+        my_tiles = (b - a + FINE_TILE - 1) / FINE_TILE;
+    }
+    {
+        uint64_t total;
+        const uint64_t ex = block_excl_scan(my_tiles, &total, sh_scan);
+        if (d0 < R1) tpre[d0] = (uint32_t)ex;
+        if (d0 == 0) tpre[R1] = (uint32_t)total;
+    }
+    __syncthreads();
+    const uint32_t W = tpre[R1];
+    for (uint32_t wi = blockIdx.x; wi < W; wi += gridDim.x) {
+        int lo = 0, hi = R1;  // largest d with tpre[d] <= wi
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (tpre[mid] <= wi) lo = mid;
+            else hi = mid;
+        }
+        const int d = lo;
+        const int64_t fb0 = (int64_t)d << cs;
+        const int64_t fe = fb0 + (1ll << cs);
+        const uint32_t ra = bstart[fb0], rb_ = bstart[fe < B ? fe : B];
+        const uint32_t r0 = ra + (wi - tpre[d]) * FINE_TILE;
+        const uint32_t r1 = min(r0 + (uint32_t)FINE_TILE, rb_);
+        hist[threadIdx.x] = 0;
+        __syncthreads();
+        ulonglong2 x[FINE_RPT];
+        uint16_t rk[FINE_RPT];
+        uint8_t dg[FINE_RPT];
+#pragma unroll
+        for (int k = 0; k < FINE_RPT; ++k) {
+            const uint32_t r = r0 + threadIdx.x + k * SORT_THREADS;
+            rk[k] = 0xFFFF;
+            dg[k] = 0;
+            if (r < r1) {
+                x[k] = load_rec2<RB>(p.rec_tmp, r);
+                const Rec rr{x[k].x, x[k].y};
+                dg[k] = (uint8_t)rec_get(rr, f.off_fb, cs);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < FINE_RPT; ++k)
+            if (r0 + threadIdx.x + k * SORT_THREADS < r1) rk[k] = (uint16_t)atomicAdd(&hist[dg[k]], 1u);
+        __syncthreads();
+        const int nd_ = 1 << cs;
+        const uint32_t n_tile = tile_scan(hist, dof, nd_, sh_scan);
+        if (threadIdx.x < nd_ && hist[threadIdx.x])
+            gbase[threadIdx.x] = atomicAdd(&p.gcur[fb0 + threadIdx.x], hist[threadIdx.x]);
+#pragma unroll
+        for (int k = 0; k < FINE_RPT; ++k) {
+            if (rk[k] == 0xFFFF) continue;
+            const uint32_t q = dof[dg[k]] + rk[k];
+            out[q] = x[k];
+            odig[q] = dg[k];
+        }
+        __syncthreads();
+        for (uint32_t q = threadIdx.x; q < n_tile; q += SORT_THREADS) {
+            const uint32_t dd = odig[q];
+            const uint64_t pos = (uint64_t)gbase[dd] + (q - dof[dd]);
+            if (pos < p.rec_cap) store_rec<RB>(p.rec, pos, out[q]);
+        }
+        __syncthreads();
+    }
+}
+
 // Per bucket b: total records = sum over CTAs of hist[c][b]; bucket starts by
 // a lookback scan over tiles of buckets; each bucket's write cursor starts at
 // its start.
@@ -281,6 +514,7 @@ __global__ void __launch_bounds__(OFFSETS_THREADS) k_offsets(OffsetsParams p) {
         const uint64_t run = sh_base + ex;
         p.bstart[b] = (uint32_t)min(run, p.rec_cap);
         p.gcur[b] = (uint32_t)min(run, p.rec_cap);
+        if (p.cshift > 0 && (b & ((1ll << p.cshift) - 1)) == 0) p.gcur_coarse[b >> p.cshift] = (uint32_t)min(run, p.rec_cap);
         if (b == B - 1) p.bstart[B] = (uint32_t)min(run + tot, p.rec_cap);
     }
 }
@@ -295,6 +529,16 @@ cudaError_t part_t(const EmitParams& p, cudaStream_t s) {
     if (p.fmt.rb == 8) k_part<TYPE, 8><<<p.n_cta_part, PART_THREADS, 0, s>>>(p);
     else k_part<TYPE, 16><<<p.n_cta_part, PART_THREADS, 0, s>>>(p);
     return cudaGetLastError();
+}
+
+template <int TYPE>
+cudaError_t set_sorted_smem() {
+    cudaError_t e = cudaFuncSetAttribute(k_part_coarse<TYPE, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)coarse_smem<TYPE>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_part_coarse<TYPE, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)coarse_smem<TYPE>());
+    return e;
 }
 
 template <int TYPE>
@@ -324,6 +568,28 @@ cudaError_t launch_part(const EmitParams& p, cudaStream_t s) {
     }
 }
 
+template <int TYPE>
+cudaError_t part_sorted_t(const EmitParams& p, const uint32_t* bstart, int grid_fine, cudaStream_t s) {
+    const size_t smem = coarse_smem<TYPE>();
+    if (p.fmt.rb == 8) k_part_coarse<TYPE, 8><<<p.n_cta_part, SORT_THREADS, smem, s>>>(p);
+    else k_part_coarse<TYPE, 16><<<p.n_cta_part, SORT_THREADS, smem, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || p.fmt.cshift <= 0) return e;
+    if (p.fmt.rb == 8) k_part_fine<8><<<grid_fine, SORT_THREADS, FINE_SMEM, s>>>(p, bstart);
+    else k_part_fine<16><<<grid_fine, SORT_THREADS, FINE_SMEM, s>>>(p, bstart);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_part_sorted(const EmitParams& p, const uint32_t* bstart, int grid_fine, cudaStream_t s) {
+    switch (p.type) {
+        case NN_TRI: return part_sorted_t<NN_TRI>(p, bstart, grid_fine, s);
+        case NN_QUAD: return part_sorted_t<NN_QUAD>(p, bstart, grid_fine, s);
+        case NN_TET: return part_sorted_t<NN_TET>(p, bstart, grid_fine, s);
+        case NN_HEX: return part_sorted_t<NN_HEX>(p, bstart, grid_fine, s);
+        default: return part_sorted_t<NN_MIXED>(p, bstart, grid_fine, s);
+    }
+}
+
 cudaError_t launch_offsets(const OffsetsParams& p, cudaStream_t s) {
     const int64_t tiles = (p.n_buckets + OFFSETS_THREADS - 1) / OFFSETS_THREADS;
     if (tiles == 0) return cudaSuccess;
@@ -332,7 +598,16 @@ cudaError_t launch_offsets(const OffsetsParams& p, cudaStream_t s) {
 }
 
 cudaError_t set_emit_smem_all(size_t bytes) {
-    cudaError_t e = set_emit_smem<NN_TRI>(bytes);
+    cudaError_t e = set_sorted_smem<NN_TRI>();
+    if (e == cudaSuccess) e = set_sorted_smem<NN_QUAD>();
+    if (e == cudaSuccess) e = set_sorted_smem<NN_TET>();
+    if (e == cudaSuccess) e = set_sorted_smem<NN_HEX>();
+    if (e == cudaSuccess) e = set_sorted_smem<NN_MIXED>();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_part_fine<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FINE_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_part_fine<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FINE_SMEM);
+    if (e == cudaSuccess) e = set_emit_smem<NN_TRI>(bytes);
     if (e == cudaSuccess) e = set_emit_smem<NN_QUAD>(bytes);
     if (e == cudaSuccess) e = set_emit_smem<NN_TET>(bytes);
     if (e == cudaSuccess) e = set_emit_smem<NN_HEX>(bytes);

@@ -24,6 +24,13 @@ struct RecFmt {
     int off_nf, off_e, eb;
     int off_n, nb;
     int rb;  // 8 or 16
+    // Partition: cshift < 0 -> one scattered pass (one store per record);
+    // cshift == 0 -> one tile-sorted pass with the bucket as radix digit
+    // (at most 256 buckets); cshift > 0 -> a tile-sorted pass on the coarse
+    // digit (bucket >> cshift) into a temporary array, then a tile-sorted
+    // pass per coarse region on the fine digit, stored in the record at off_fb.
+    int cshift;
+    int off_fb;
 };
 
 // Element walk: the kernels that read the connectivity (histogram and
@@ -41,6 +48,8 @@ struct EmitParams {
     int n_cta_part;   // CTAs of the partition pass
     uint32_t* hist;   // [n_cta][n_buckets] record counts of each CTA's element slice
     uint32_t* gcur;   // [n_buckets] write cursor of each bucket (starts at the bucket start)
+    uint32_t* gcur_coarse;  // [256] write cursor of each coarse region (two-level partition)
+    uint8_t* rec_tmp; // records grouped by coarse region (two-level partition)
     uint8_t* rec;     // records, grouped by bucket
     uint64_t rec_cap; // records that fit; more only when elem_ptr is invalid
     int32_t* status;
@@ -54,6 +63,8 @@ struct OffsetsParams {
     int64_t n_buckets;
     uint32_t* bstart;       // [n_buckets+1] first record of each bucket
     uint32_t* gcur;         // [n_buckets] set to the bucket starts
+    uint32_t* gcur_coarse;  // [256] set to the coarse region starts (when cshift > 0)
+    int cshift;
     uint64_t* lb_state;     // lookback words, one per tile of buckets
     uint32_t* ticket;
     uint64_t rec_cap;       // bucket starts are clamped to the record array
@@ -118,11 +129,13 @@ struct BucketParams {
 
 constexpr int EMIT_THREADS = 1024;
 constexpr int PART_THREADS = 512;
+constexpr int SORT_THREADS = 256;   // tile-sorted partition passes
 constexpr int OFFSETS_THREADS = 128;
 
 // launchers (return the CUDA error of the launch)
 cudaError_t launch_hist(const EmitParams& p, size_t smem, cudaStream_t s);
 cudaError_t launch_part(const EmitParams& p, cudaStream_t s);
+cudaError_t launch_part_sorted(const EmitParams& p, const uint32_t* bstart, int grid_fine, cudaStream_t s);
 cudaError_t launch_offsets(const OffsetsParams& p, cudaStream_t s);
 cudaError_t launch_bucket(const BucketParams& p, int grid, int threads, size_t smem, cudaStream_t s);
 cudaError_t launch_batch_emit(const BatchTables& bt, uint32_t* bcount, uint32_t* gcur, uint8_t* rec,

@@ -85,6 +85,24 @@ def test_parity_spill_path(name):
     check_against_oracle(m, nn.WANT_BOTH, b, ws_extra=64 * m.n_conn)
 
 
+@pytest.mark.parametrize("name", ["tri300_holes", "tet41", "hex61", "mixed41"])
+def test_parity_scattered_partition(name):
+    """The one-pass partition with one scattered store per record (the fallback
+    when the fine-digit field does not fit the record)."""
+    with env(NN_PART="scatter"):
+        b = nn.Builder()
+    check_against_oracle(MESHES[name](), nn.WANT_BOTH, b)
+
+
+@pytest.mark.parametrize("sb", [4, 6])
+def test_parity_two_level_partition_many_buckets(sb):
+    """Narrow buckets: thousands of buckets, coarse regions of up to 2^cshift buckets."""
+    with env(NN_SB=sb):
+        b = nn.Builder()
+    m = mg.tet_grid(61, 31)
+    check_against_oracle(m, nn.WANT_BOTH, b, ws_extra=64 * m.n_conn)
+
+
 def fan(n_tri, hub=0, extra_nodes=3):
     """A closed fan of n_tri triangles around the hub (valence n_tri) plus isolated nodes."""
     el = [(mg.TRI, (hub, 1 + k, 1 + (k + 1) % n_tri)) for k in range(n_tri)]
