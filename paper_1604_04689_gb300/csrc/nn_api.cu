@@ -23,6 +23,7 @@ struct nn_handle {
     size_t smem_per_sm = 0;
     int sb_override = -1;      // fixed bucket width (tests / tuning), -1 = automatic
     int part_mode = -1;        // -1 automatic, 0 one scattered store per record (tests)
+    int64_t hist_chunk_override = 0;  // > 0: count at most this many buckets per walk (tests)
     // per-stage timing (nn_profile_*)
     bool prof = false;
     bool pending = false;
@@ -53,6 +54,7 @@ struct Plan {
     int64_t N = 0, T = 0, n_conn = 0;
     RecFmt fmt{};
     int64_t B = 0;
+    int64_t hist_chunk = 1;
     int G = 1;
     int G_part = 1;
     int G_fine = 1;
@@ -96,21 +98,21 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     const double inc = p.N > 0 ? (double)p.n_conn / (double)p.N : 0.0;
     const double E = (want & NN_WANT_ELEMS) ? inc : 0.0;
     const double C = (want & NN_WANT_NODES) ? p.k * inc : 0.0;
-    double Tt = 0.0;
-    if (C > 0) {
-        Tt = 2;
-        while (Tt <= std::ceil(C)) Tt *= 2;
-    }
-    const double per_node = 4.0 * (E + Tt + 0.5 * C);  // list + table + staged row, bytes
+    const double Tt = C > 0 ? C + 1.0 : 0.0;
+    const double per_node = 4.0 * (E + 2.0 * Tt);  // element list + hash table + distinct list, bytes
     // prefer a shared-memory size that lets two bucket CTAs share an SM, so one
     // CTA's barriers and lookback waits overlap the other's memory traffic
+    // (many buckets are fine: the histogram pass counts them in chunks that fit
+    // its shared memory; the hard cap below only bounds workspace tables)
+    const int64_t B_lim = (int64_t)1 << 20;
     int sb = -1;
     size_t bsmem = std::min(h->bucket_smem, h->smem_per_sm / 2 - 2048);
     for (int pass = 0; pass < 2 && sb < 0; ++pass) {
         if (pass == 1) bsmem = h->bucket_smem;
         for (int s = SB_MAX; s >= SB_MIN + 2; --s) {
+            if (((p.N + (1ll << s) - 1) >> s) > B_lim) break;
             const double area = (double)bsmem - (double)BUCKET_FIXED_PER_NODE * (1 << s) - BUCKET_FIXED;
-            if (area > 0 && (double)(1 << s) * per_node <= 0.6 * area) {
+            if (area > 0 && (double)(1 << s) * per_node <= 0.8 * area) {
                 sb = s;
                 break;
             }
@@ -126,7 +128,7 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     auto fixed_of = [](int s) { return BUCKET_FIXED_PER_NODE * ((size_t)1 << s) + BUCKET_FIXED; };
     const size_t min_area = 4096 * 4;
     while (sb > SB_MIN && fixed_of(sb) + min_area > p.bucket_smem) --sb;
-    const int64_t B_max = (int64_t)((h->smem_optin - 1024) / 4);
+    const int64_t B_max = B_lim;
     auto nbk = [&](int s) { return (p.N + (1ll << s) - 1) >> s; };
     while (nbk(sb) > B_max && sb < SB_MAX) ++sb;
     if (nbk(sb) > B_max || fixed_of(sb) + min_area > p.bucket_smem) return NN_ERR_ARG;
@@ -149,7 +151,7 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     while (((p.B + (1ll << cs) - 1) >> cs) > 256) ++cs;
     f.cshift = -1;
     f.off_fb = total;
-    if (h->part_mode != 0 && total + cs <= 128) {
+    if (h->part_mode != 0 && total + cs <= 128 && cs <= 12) {  // <= 4096 buckets per coarse region
         f.cshift = cs;
         total += cs;
     }
@@ -158,7 +160,9 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     // element-walk CTAs: one or two per SM, each a fixed slice of elements
     const int unit = p.type == NN_TRI ? 4 : 1;
     const int64_t n_units = (p.T + unit - 1) / unit;
-    p.emit_smem = std::max<size_t>(16, (size_t)p.B * 4);
+    p.hist_chunk = std::min<int64_t>(p.B, (int64_t)((h->smem_optin - 1024) / 4));
+    if (h->hist_chunk_override > 0) p.hist_chunk = std::min<int64_t>(p.hist_chunk, h->hist_chunk_override);
+    p.emit_smem = std::max<size_t>(16, (size_t)p.hist_chunk * 4);
     const int cps = p.emit_smem + 2048 <= 113 * 1024 ? 2 : 1;
     p.G = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sms * cps, (n_units + 2047) / 2048));
     p.G_part = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sms * 2, (n_units + 511) / 512));
@@ -246,6 +250,7 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
     ep.elem_type = m->elem_type;
     ep.fmt = p.fmt;
     ep.n_buckets = p.B;
+    ep.hist_chunk = std::max<int64_t>(1, p.hist_chunk);
     ep.n_cta = p.G;
     ep.n_cta_part = p.G_part;
     ep.hist = reinterpret_cast<uint32_t*>(w + p.off_hist);
@@ -541,6 +546,7 @@ nn_status nn_create(nn_handle** out) {
     h->bucket_smem = h->smem_optin - 1024;  // the bucket kernel has a little static shared memory
     if (const char* e = std::getenv("NN_SB")) h->sb_override = std::atoi(e);
     if (const char* e = std::getenv("NN_PART")) h->part_mode = std::strcmp(e, "scatter") == 0 ? 0 : -1;
+    if (const char* e = std::getenv("NN_HIST_CHUNK")) h->hist_chunk_override = std::atoll(e);
     if (const char* e = std::getenv("NN_BUCKET_SMEM_KB")) {
         size_t kb = (size_t)std::atol(e);
         if (kb >= 32 && kb * 1024 <= h->smem_optin - 1024) h->bucket_smem = kb * 1024;

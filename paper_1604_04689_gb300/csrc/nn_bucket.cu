@@ -2,10 +2,11 @@
 //
 // For the 2^sb nodes of a bucket the CTA counts, per node, the element
 // entries and the neighbour candidates of its records; lays out one element
-// list and one open-addressing hash table per node in shared memory (table
-// size = next power of two above the candidate count, so it never fills);
-// inserts the candidates (a repeated neighbour -- an edge shared by several
-// elements -- hits its own slot and is dropped); sorts each row; and writes
+// list, one open-addressing hash table (one slot more than the node has
+// candidates, so it never fills) and one list of distinct neighbours per node
+// in shared memory; inserts the candidates (a repeated neighbour -- an edge
+// shared by several elements -- hits its own slot and is dropped, a new one is
+// appended to the node's list); sorts each row by ranking; and writes
 // row_ptr and col of both CSRs at offsets found by a lookback scan over the
 // buckets, which are processed in node order.  A bucket whose lists and
 // tables do not fit shared memory keeps its tables in a global spill area
@@ -40,13 +41,14 @@ __device__ __forceinline__ Rec load_rec(const uint8_t* base, uint32_t r) {
     return x;
 }
 
-// Insert x into the open-addressing table tab[0..mask]; true if x was new.
-// The table has more slots than distinct values ever inserted; the probe
-// count is still bounded and an overrun reports NN_ERR_WORKSPACE.
-__device__ __forceinline__ bool tab_insert(uint32_t* tab, uint32_t mask, int shift, uint32_t x,
-                                           int32_t* status) {
-    uint32_t h = (x * 0x9E3779B1u) >> shift;
-    for (uint32_t probes = 0; probes <= mask; ++probes) {
+// Insert x into the open-addressing table tab[0..T); true if x was new.  T is
+// larger than the number of distinct values ever inserted (T = candidates + 1),
+// so a free slot always exists; the probe count is still bounded and an
+// overrun reports NN_ERR_WORKSPACE.  The start slot is the high word of
+// hash(x) * T (a multiply-shift range reduction onto [0, T)).
+__device__ __forceinline__ bool tab_insert(uint32_t* tab, uint32_t T, uint32_t x, int32_t* status) {
+    uint32_t h = __umulhi(x * 0x9E3779B1u, T);
+    for (uint32_t probes = 0; probes < T; ++probes) {
         uint32_t cur = *reinterpret_cast<volatile uint32_t*>(&tab[h]);
         if (cur == x) return false;
         if (cur == EMPTY) {
@@ -54,30 +56,13 @@ __device__ __forceinline__ bool tab_insert(uint32_t* tab, uint32_t mask, int shi
             if (old == EMPTY) return true;
             if (old == x) return false;
         }
-        h = (h + 1) & mask;
+        h = h + 1 == T ? 0 : h + 1;
     }
     set_status(status, NN_ERR_WORKSPACE);
     return false;
 }
 
-// Row of entry i: the largest l with off[l] <= i (off is a non-decreasing
-// exclusive scan with off[0] = 0, so empty rows are skipped).
-__device__ __forceinline__ int row_of(const uint32_t* off, int n, uint32_t i) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (off[mid] <= i) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo - 1;
-}
-
-__device__ __forceinline__ uint32_t table_size(uint32_t c) {
-    if (c == 0) return 0;
-    uint32_t t = 2;
-    while (t <= c && t < 0x80000000u) t <<= 1;  // smallest power of two > c
-    return t;
-}
+__device__ __forceinline__ uint32_t table_size(uint32_t c) { return c == 0 ? 0 : (c < 0xFFFFFFFEu ? c + 1 : c); }
 
 struct BucketOut {
     int64_t n_nodes, first;
@@ -195,14 +180,14 @@ __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
         __syncthreads();
         const uint64_t Tb = smem_array_excl_scan(cnt, NB, sh_scan);
         for (int l = tid; l < NB; l += BS) toff[l] = (uint32_t)cnt[l];
-        const bool fast_b = Eb + Tb <= p.area_words;
+        const bool fast_b = Eb + 2 * Tb <= p.area_words;  // element lists, tables, unique lists
         if (want_e && tid == 0) lb_publish(p.lb_e, b, Eb, first);
         if (tid < 32) {  // large buckets write element lists straight to the output: need the offset now
             const uint64_t ge = (want_e && !fast_b) ? lb_resolve(p.lb_e, b, Eb, status, first) : 0;
             if (tid == 0) misc[1] = ge;
         }
         if (tid == 0) {
-            const bool fast = fast_b;
+            const bool fast = fast_b;  // else: tables in the spill area, rows gathered from them
             uint64_t spill_off = 0;
             bool tab_ok = true;
             if (!fast && want_n && Tb > 0) {
@@ -222,6 +207,7 @@ __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
         uint32_t* elist = fast ? area : reinterpret_cast<uint32_t*>(sh_out.col_e) + Ge;
         const bool e_write = want_e && (fast || e_ok);
         uint32_t* tab = fast ? area + Eb : p.spill + misc[2];
+        uint32_t* ulist = fast ? area + Eb + Tb : nullptr;  // distinct neighbours of node l at ulist[toff[l]..]
         if (tab_ok)
             for (uint64_t i = tid; i < Tb; i += BS) tab[i] = EMPTY;
         __syncthreads();
@@ -242,13 +228,15 @@ __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
                 elist[eoff[vloc] + q] = rec_get(x, f.off_e, f.eb);
             }
             if (tab_ok) {
-                const uint32_t T = tsz[vloc];
-                uint32_t* t = tab + toff[vloc];
-                const int shift = __clz(T) + 1;
+                const uint32_t T = tsz[vloc], o = toff[vloc];
+                uint32_t* t = tab + o;
 #pragma unroll
                 for (int s = 0; s < K; ++s) {
                     const uint32_t y = rec_get(x, f.off_n + s * f.nb, f.nb);
-                    if (y && tab_insert(t, T - 1, shift, y - 1, status)) atomicAdd(&ucnt[vloc], 1u);
+                    if (y && tab_insert(t, T, y - 1, status)) {
+                        const uint32_t pos = atomicAdd(&ucnt[vloc], 1u);
+                        if (ulist) ulist[o + pos] = y - 1;
+                    }
                 }
             }
           }
@@ -259,6 +247,7 @@ __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
         const uint64_t Ub = smem_array_excl_scan(cnt, NB, sh_scan);
         for (int l = tid; l < NB; l += BS) aux[l] = (uint32_t)cnt[l];
         if (want_n && tid == 0) lb_publish(p.lb_n, b, Ub, first);
+        __syncthreads();  // row offsets (aux) are read across threads below
         uint64_t Gn = 0;
         bool n_ok = false;
         // output offsets of this bucket: resolved now for large buckets (they
@@ -290,60 +279,44 @@ __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
             }
         };
 
-        // rows: gather each node's distinct neighbours from its table, sort
-        uint32_t* stage = (fast && Eb + Tb + Ub <= p.area_words) ? area + Eb + Tb : nullptr;
+        // rows: each node's distinct neighbours are in its unique list (fast
+        // buckets); rank-sort every row, four threads per node
+        uint32_t* stage = (fast && Eb + 2 * Tb + Ub <= p.area_words) ? area + Eb + 2 * Tb : nullptr;
         uint32_t* sorted = nullptr;
-        if (stage) {
-            if (Ub + Eb <= Tb) sorted = tab;  // the tables are dead once gathered
-            else if (Eb + Tb + 2 * Ub + Eb <= p.area_words) sorted = stage + Ub;
+        if (fast) {
+            if (Ub + Eb <= Tb) sorted = tab;  // the tables are dead after the second pass
+            else if (Eb + 2 * Tb + Ub + Eb <= p.area_words) sorted = area + Eb + 2 * Tb;
         }
         if (sorted) {
-            // gather: four threads per node, starting at bank-staggered slots
-            uint32_t* fill = reinterpret_cast<uint32_t*>(cnt);
-            for (int l = tid; l < NB; l += BS) fill[l] = 0;
-            __syncthreads();
-            if (tab_ok) {
-                for (int idx = tid; idx < NB * 4; idx += BS) {
-                    const int l = idx >> 2;
-                    const uint32_t T = tsz[l];
-                    const uint32_t* t = tab + toff[l];
-                    const uint32_t dst = aux[l], st = 4u * (uint32_t)l;
-                    for (uint32_t q = idx & 3; q < T; q += 4) {
-                        const uint32_t y = t[(q + st) & (T - 1)];
-                        if (y != EMPTY) stage[dst + atomicAdd(&fill[l], 1u)] = y;
-                    }
-                }
-            }
-            __syncthreads();
-            // sort each row by rank (every entry counts the smaller entries of its row)
             int has_long = 0;
             uint32_t* sorted_e = sorted + Ub;
-            if (tab_ok) {
-                for (uint32_t i = tid; i < Ub; i += BS) {
-                    const int l = row_of(aux, NB, i);
-                    const uint32_t a = aux[l], U = ucnt[l], x = stage[i];
-                    uint32_t rank = i - a;
-                    if (U <= RANK_MAX) {
-                        rank = 0;
-                        for (uint32_t j = a; j < a + U; ++j) rank += stage[j] < x;
-                    } else {
-                        has_long = 1;
+            for (int idx = tid; idx < NB * 4; idx += BS) {
+                const int l = idx >> 2, part = idx & 3;
+                if (tab_ok) {
+                    const uint32_t U = ucnt[l], a = toff[l], o = aux[l];
+                    if (U > RANK_MAX) has_long = 1;
+                    for (uint32_t j = part; j < U; j += 4) {
+                        const uint32_t x = ulist[a + j];
+                        uint32_t rank = j;
+                        if (U <= RANK_MAX) {
+                            rank = 0;
+                            for (uint32_t i = 0; i < U; ++i) rank += ulist[a + i] < x;
+                        }
+                        sorted[o + rank] = x;
                     }
-                    sorted[a + rank] = x;
                 }
-            }
-            if (want_e) {
-                for (uint32_t i = tid; i < Eb; i += BS) {
-                    const int l = row_of(eoff, NB, i);
-                    const uint32_t a = eoff[l], E = (l + 1 < NB ? eoff[l + 1] : (uint32_t)Eb) - a, x = elist[i];
-                    uint32_t rank = i - a;
-                    if (E <= RANK_MAX) {
-                        rank = 0;
-                        for (uint32_t j = a; j < a + E; ++j) rank += elist[j] < x;
-                    } else {
-                        has_long = 1;
+                if (want_e) {
+                    const uint32_t a = eoff[l], E = (l + 1 < NB ? eoff[l + 1] : (uint32_t)Eb) - a;
+                    if (E > RANK_MAX) has_long = 1;
+                    for (uint32_t j = part; j < E; j += 4) {
+                        const uint32_t x = elist[a + j];
+                        uint32_t rank = j;
+                        if (E <= RANK_MAX) {
+                            rank = 0;
+                            for (uint32_t i = 0; i < E; ++i) rank += elist[a + i] < x;
+                        }
+                        sorted_e[a + rank] = x;
                     }
-                    sorted_e[a + rank] = x;
                 }
             }
             has_long = __syncthreads_or(has_long);
@@ -375,7 +348,7 @@ __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
                     const uint32_t T = tsz[l];
                     uint32_t j = 0;
                     for (uint32_t q = 0; q < T; ++q) {
-                        const uint32_t y = t[(q + (uint32_t)l) & (T - 1)];
+                        const uint32_t y = t[q];
                         if (y != EMPTY) d[j++] = y;
                     }
                     if (U <= LONG_ROW) insertion_sort(d, (int)U);

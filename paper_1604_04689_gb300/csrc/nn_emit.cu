@@ -100,19 +100,27 @@ __device__ __forceinline__ void walk_cta(const EmitParams& p, F&& f) {
     }
 }
 
+// Counts per bucket of this CTA's element slice, in shared memory.  When the
+// buckets outnumber the shared counters (hist_chunk), the slice is walked once
+// per chunk of buckets.
 template <int TYPE>
 __global__ void __launch_bounds__(EMIT_THREADS) k_hist(EmitParams p) {
     extern __shared__ uint32_t sh_hist[];
     const int64_t B = p.n_buckets;
-    for (int64_t b = threadIdx.x; b < B; b += blockDim.x) sh_hist[b] = 0;
-    __syncthreads();
     const int sb = p.fmt.sb;
-    walk_cta<TYPE>(p, [&](int32_t v, int, int64_t, int32_t, int32_t, int32_t) {
-        atomicAdd(&sh_hist[v >> sb], 1u);
-    });
-    __syncthreads();
     uint32_t* row = p.hist + (int64_t)blockIdx.x * B;
-    for (int64_t b = threadIdx.x; b < B; b += blockDim.x) row[b] = sh_hist[b];
+    for (int64_t c0 = 0; c0 < B; c0 += p.hist_chunk) {
+        const int64_t nc = min(B - c0, p.hist_chunk);
+        for (int64_t b = threadIdx.x; b < nc; b += blockDim.x) sh_hist[b] = 0;
+        __syncthreads();
+        walk_cta<TYPE>(p, [&](int32_t v, int, int64_t, int32_t, int32_t, int32_t) {
+            const int64_t b = (int64_t)(v >> sb) - c0;
+            if (b >= 0 && b < nc) atomicAdd(&sh_hist[b], 1u);
+        });
+        __syncthreads();
+        for (int64_t b = threadIdx.x; b < nc; b += blockDim.x) row[c0 + b] = sh_hist[b];
+        __syncthreads();
+    }
 }
 
 // Load one work unit (4 triangles or one element); returns the runtime type
@@ -262,6 +270,23 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_part(EmitParams p) {
 // contiguously, so global stores are coalesced runs instead of one scattered
 // 16-byte store per record.
 
+// Exclusive scan of hist[0..n) (any n) into dof, a contiguous chunk per thread;
+// returns the total.  Ends with a barrier: any thread may read any dof entry.
+__device__ __forceinline__ uint32_t tile_scan_n(const uint32_t* hist, uint32_t* dof, int n, uint64_t* sh) {
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int lo = min(n, (int)threadIdx.x * per), hi = min(n, lo + per);
+    uint64_t x = 0;
+    for (int i = lo; i < hi; ++i) x += hist[i];
+    uint64_t total;
+    uint64_t run = block_excl_scan(x, &total, sh);
+    for (int i = lo; i < hi; ++i) {
+        dof[i] = (uint32_t)run;
+        run += hist[i];
+    }
+    __syncthreads();
+    return (uint32_t)total;
+}
+
 // Exclusive scan of hist[0..n) (n <= blockDim.x) into dof; returns the total.
 // Ends with a barrier: every thread may read any dof entry afterwards.
 __device__ __forceinline__ uint32_t tile_scan(const uint32_t* hist, uint32_t* dof, int n, uint64_t* sh) {
@@ -289,7 +314,10 @@ __host__ __device__ constexpr size_t coarse_smem() {
 }
 constexpr int FINE_RPT = 4;
 constexpr int FINE_TILE = SORT_THREADS * FINE_RPT;
-constexpr size_t FINE_SMEM = (size_t)FINE_TILE * 17 + 3 * 256 * 4 + 257 * 4;
+constexpr int FINE_DIGITS = 4096;  // buckets per coarse region: at most 256 x 4096 buckets in all
+// shared memory of the fine pass for nd digits per coarse region
+__host__ __device__ constexpr size_t fine_smem(int nd) { return (size_t)FINE_TILE * 18 + 3 * (size_t)nd * 4 + 257 * 4; }
+constexpr size_t FINE_SMEM = fine_smem(FINE_DIGITS);
 
 template <int TYPE>
 __device__ __forceinline__ Rec make_rec(const RecFmt& f, const int32_t* e_nd, int i, int t, int64_t e) {
@@ -408,14 +436,15 @@ template <int RB>
 __global__ void __launch_bounds__(SORT_THREADS) k_part_fine(EmitParams p, const uint32_t* bstart) {
     extern __shared__ __align__(16) uint8_t sm[];
     ulonglong2* out = reinterpret_cast<ulonglong2*>(sm);
-    uint8_t* odig = reinterpret_cast<uint8_t*>(out + FINE_TILE);
-    uint32_t* hist = reinterpret_cast<uint32_t*>(odig + FINE_TILE);
-    uint32_t* dof = hist + 256;
-    uint32_t* gbase = dof + 256;
-    uint32_t* tpre = gbase + 256;  // [257] first tile of each coarse region
-    __shared__ uint64_t sh_scan[34];
+    uint16_t* odig = reinterpret_cast<uint16_t*>(out + FINE_TILE);
     const RecFmt f = p.fmt;
     const int cs = f.cshift;
+    const int nd_ = 1 << cs;  // digits (buckets) per coarse region, <= FINE_DIGITS
+    uint32_t* hist = reinterpret_cast<uint32_t*>(odig + FINE_TILE);
+    uint32_t* dof = hist + nd_;
+    uint32_t* gbase = dof + nd_;
+    uint32_t* tpre = gbase + nd_;  // [257] first tile of each coarse region
+    __shared__ uint64_t sh_scan[34];
     const int64_t B = p.n_buckets;
     const int R1 = (int)((B + (1ll << cs) - 1) >> cs);
     const int d0 = threadIdx.x;
@@ -447,11 +476,11 @@ __global__ void __launch_bounds__(SORT_THREADS) k_part_fine(EmitParams p, const 
         const uint32_t ra = bstart[fb0], rb_ = bstart[fe < B ? fe : B];
         const uint32_t r0 = ra + (wi - tpre[d]) * FINE_TILE;
         const uint32_t r1 = min(r0 + (uint32_t)FINE_TILE, rb_);
-        hist[threadIdx.x] = 0;
+        for (int i = threadIdx.x; i < nd_; i += SORT_THREADS) hist[i] = 0;
         __syncthreads();
         ulonglong2 x[FINE_RPT];
         uint16_t rk[FINE_RPT];
-        uint8_t dg[FINE_RPT];
+        uint16_t dg[FINE_RPT];
 #pragma unroll
         for (int k = 0; k < FINE_RPT; ++k) {
             const uint32_t r = r0 + threadIdx.x + k * SORT_THREADS;
@@ -460,17 +489,16 @@ __global__ void __launch_bounds__(SORT_THREADS) k_part_fine(EmitParams p, const 
             if (r < r1) {
                 x[k] = load_rec2<RB>(p.rec_tmp, r);
                 const Rec rr{x[k].x, x[k].y};
-                dg[k] = (uint8_t)rec_get(rr, f.off_fb, cs);
+                dg[k] = (uint16_t)rec_get(rr, f.off_fb, cs);
             }
         }
 #pragma unroll
         for (int k = 0; k < FINE_RPT; ++k)
             if (r0 + threadIdx.x + k * SORT_THREADS < r1) rk[k] = (uint16_t)atomicAdd(&hist[dg[k]], 1u);
         __syncthreads();
-        const int nd_ = 1 << cs;
-        const uint32_t n_tile = tile_scan(hist, dof, nd_, sh_scan);
-        if (threadIdx.x < nd_ && hist[threadIdx.x])
-            gbase[threadIdx.x] = atomicAdd(&p.gcur[fb0 + threadIdx.x], hist[threadIdx.x]);
+        const uint32_t n_tile = tile_scan_n(hist, dof, nd_, sh_scan);
+        for (int i = threadIdx.x; i < nd_; i += SORT_THREADS)
+            if (hist[i]) gbase[i] = atomicAdd(&p.gcur[fb0 + i], hist[i]);
 #pragma unroll
         for (int k = 0; k < FINE_RPT; ++k) {
             if (rk[k] == 0xFFFF) continue;
@@ -575,8 +603,9 @@ cudaError_t part_sorted_t(const EmitParams& p, const uint32_t* bstart, int grid_
     else k_part_coarse<TYPE, 16><<<p.n_cta_part, SORT_THREADS, smem, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || p.fmt.cshift <= 0) return e;
-    if (p.fmt.rb == 8) k_part_fine<8><<<grid_fine, SORT_THREADS, FINE_SMEM, s>>>(p, bstart);
-    else k_part_fine<16><<<grid_fine, SORT_THREADS, FINE_SMEM, s>>>(p, bstart);
+    const size_t fs = fine_smem(1 << p.fmt.cshift);
+    if (p.fmt.rb == 8) k_part_fine<8><<<grid_fine, SORT_THREADS, fs, s>>>(p, bstart);
+    else k_part_fine<16><<<grid_fine, SORT_THREADS, fs, s>>>(p, bstart);
     return cudaGetLastError();
 }
 

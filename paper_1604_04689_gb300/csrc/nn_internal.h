@@ -44,6 +44,7 @@ struct EmitParams {
     const uint8_t* elem_type;
     RecFmt fmt;
     int64_t n_buckets;
+    int64_t hist_chunk;  // buckets counted per walk of the histogram pass (shared counters)
     int n_cta;        // CTAs of the histogram pass (rows of hist)
     int n_cta_part;   // CTAs of the partition pass
     uint32_t* hist;   // [n_cta][n_buckets] record counts of each CTA's element slice

@@ -103,6 +103,14 @@ def test_parity_two_level_partition_many_buckets(sb):
     check_against_oracle(m, nn.WANT_BOTH, b, ws_extra=64 * m.n_conn)
 
 
+@pytest.mark.parametrize("chunk", [1, 37, 100])
+def test_parity_histogram_in_chunks(chunk):
+    """More buckets than shared counters: the histogram walks the elements once per chunk."""
+    with env(NN_HIST_CHUNK=chunk, NN_SB=6):
+        b = nn.Builder()
+    check_against_oracle(MESHES["mixed41"](), nn.WANT_BOTH, b, ws_extra=64 * MESHES["mixed41"]().n_conn)
+
+
 def fan(n_tri, hub=0, extra_nodes=3):
     """A closed fan of n_tri triangles around the hub (valence n_tri) plus isolated nodes."""
     el = [(mg.TRI, (hub, 1 + k, 1 + (k + 1) % n_tri)) for k in range(n_tri)]
