@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--tune", choices=["auto", "off", "sweep"], default="auto",
+                    help="launch tuning: cached or timed once (auto), planner default (off), re-timed (sweep)")
     ap.add_argument("--requests", type=int, default=10000, help="serve workload: number of requests")
     ap.add_argument("--load", type=float, default=0.8, help="serve workload: arrival rate / plain saturated rate")
     return ap.parse_args()
@@ -248,6 +250,10 @@ def main():
     mesh = make_mesh(args.workload)
     b = nn.Builder(dev)
     dm = nn.DeviceMesh.from_host(mesh, device=dev)
+    tuning = None
+    if args.tune != "off":
+        from paper_1604_04689_gb300 import autotune
+        tuning = autotune.tuned(b, dm, want, retune=args.tune == "sweep")
     ws_bytes, ncap, ecap = b.query(dm, want)
     plan = nn.nn_plan_info(b.h, dm.struct(), want)
     ws = b.workspace(ws_bytes)
@@ -345,7 +351,8 @@ def main():
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload][1],
                    "want": args.want, "n_nodes": N, "n_elems": T, "nnz": nnz,
                    "l2": f"flushed before every timed step ({flush.numel() >> 20} MiB write)",
-                   "parallelism": "replicas" if world > 1 else "single GPU", "plan": plan},
+                   "parallelism": "replicas" if world > 1 else "single GPU", "plan": plan,
+                   "tuning": tuning},
         "roofline": {"bound": "hbm", "kernel": KERNEL_OF_STAGE[dom], "achieved": achieved, "peak": peak,
                      "peak_source": f"{peak_src} copy bandwidth", "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "alg_bytes_per_launch": alg[dom], "ms_per_launch": dom_ms},
@@ -354,7 +361,7 @@ def main():
                      "frac": pipeline_bytes / (ms_per_step * 1e-3) / 1e9 / peak,
                      "stage_ms_per_step": {k: v / max(calls, 1) for k, v in stage_ms.items()},
                      "wall_s": t_wall},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": launches_per_build(plan) * args.steps,
         "clocks": clocks,
         "e2e": e2e,
         "cpu_baseline": baseline,
@@ -405,6 +412,12 @@ def end_to_end(torch, nn, b, mesh, dm, want, ws, ws_bytes, out, steps, dev, worl
     return {"value": world * mesh.n_elems * steps / dt / 1e6, "unit": "Melem/s",
             "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
             "ms_per_step": dt * 1e3 / steps}
+
+
+def launches_per_build(plan):
+    """Kernels one build launches: histogram, offsets, partition (one pass, or
+    coarse + fine when the buckets span more than 256 coarse digits), bucket."""
+    return 3 + (2 if plan["partition"] > 0 else 1)
 
 
 def source_digest():

@@ -107,11 +107,26 @@ void nn_destroy(nn_handle* h);
 nn_status nn_query(nn_handle* h, const nn_mesh* mesh, int want, size_t* ws_bytes,
                    int64_t* node_col_cap, int64_t* elem_col_cap);
 
+/* Launch tuning held by a handle, applied to its later calls (0 = the
+ * library's automatic choice).  sb: log2 of the bucket width in nodes (4..11);
+ * bucket_threads: 256 or 512 threads per bucket CTA; bucket_ctas_per_sm: 1, 2
+ * or 4 bucket CTAs sharing an SM (sets the shared memory per CTA; 4 needs 256
+ * threads).  Results never depend on tuning, only speed and workspace size.
+ * nn_set_tuning(h, NULL) restores the automatic choice. */
+typedef struct {
+    int32_t sb;
+    int32_t bucket_threads;
+    int32_t bucket_ctas_per_sm;
+} nn_tuning;
+nn_status nn_set_tuning(nn_handle* h, const nn_tuning* tuning);
+
 /* Parameters of the build plan for a mesh (host-only; for tooling and
  * traffic accounting).  Fills up to n of: info[0] bucket shift (a bucket is
  * 2^info[0] consecutive node ids), [1] number of buckets, [2] CTAs of the
  * element walk, [3] bytes per incidence record, [4] minimum workspace bytes,
- * [5] CTAs of the bucket pass. */
+ * [5] CTAs of the bucket pass, [6] threads per bucket CTA, [7] shared memory
+ * per bucket CTA, [8] partition mode (-1 scattered, 0 one sorted pass, k > 0
+ * coarse + fine sorted passes with 2^k buckets per coarse region). */
 nn_status nn_plan_info(nn_handle* h, const nn_mesh* mesh, int want, int64_t* info, int n);
 
 /* Neighbor nodes of every node (Sec. 2.1.1, Sec. 2.2.1) into *out. */

@@ -24,6 +24,7 @@ struct nn_handle {
     int sb_override = -1;      // fixed bucket width (tests / tuning), -1 = automatic
     int part_mode = -1;        // -1 automatic, 0 one scattered store per record (tests)
     int64_t hist_chunk_override = 0;  // > 0: count at most this many buckets per walk (tests)
+    nn_tuning tuning{};        // nn_set_tuning: bucket width, block size, CTAs per SM (0 = automatic)
     // per-stage timing (nn_profile_*)
     bool prof = false;
     bool pending = false;
@@ -63,6 +64,7 @@ struct Plan {
            off_ctrl = 0, off_spill = 0, zero_begin = 0, zero_end = 0;
     size_t ws_min = 0, ws_rec = 0;
     int bucket_grid = 0;
+    int bucket_threads = 512;
     size_t bucket_smem = 0;
     uint32_t area_words = 0;
 };
@@ -106,9 +108,14 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     // its shared memory; the hard cap below only bounds workspace tables)
     const int64_t B_lim = (int64_t)1 << 20;
     int sb = -1;
-    size_t bsmem = std::min(h->bucket_smem, h->smem_per_sm / 2 - 2048);
+    const int tcps = h->tuning.bucket_ctas_per_sm;  // tuned: that many bucket CTAs share an SM
+    size_t bsmem = tcps > 0 ? std::min(h->bucket_smem, h->smem_per_sm / (size_t)tcps - 2048)
+                           : std::min(h->bucket_smem, h->smem_per_sm / 2 - 2048);
     for (int pass = 0; pass < 2 && sb < 0; ++pass) {
-        if (pass == 1) bsmem = h->bucket_smem;
+        if (pass == 1) {
+            if (tcps > 0) break;
+            bsmem = h->bucket_smem;
+        }
         for (int s = SB_MAX; s >= SB_MIN + 2; --s) {
             if (((p.N + (1ll << s) - 1) >> s) > B_lim) break;
             const double area = (double)bsmem - (double)BUCKET_FIXED_PER_NODE * (1 << s) - BUCKET_FIXED;
@@ -119,6 +126,7 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
         }
     }
     if (sb < 0) sb = SB_MIN;
+    if (h->tuning.sb >= SB_MIN && h->tuning.sb <= SB_MAX) sb = h->tuning.sb;
     if (h->sb_override >= SB_MIN && h->sb_override <= SB_MAX) {
         sb = h->sb_override;
         bsmem = h->bucket_smem;
@@ -191,8 +199,9 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
 
     const size_t fixed = BUCKET_FIXED_PER_NODE * ((size_t)1 << sb) + BUCKET_FIXED;
     p.area_words = (uint32_t)((p.bucket_smem - fixed) / 4);
+    p.bucket_threads = h->tuning.bucket_threads == 256 ? 256 : bucket_threads();
     int per_sm = 1;
-    if (bucket_occupancy(&per_sm, bucket_threads(), p.bucket_smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+    if (bucket_occupancy(&per_sm, p.bucket_threads, p.bucket_smem) != cudaSuccess || per_sm < 1) per_sm = 1;
     p.bucket_grid = (int)std::min<int64_t>(p.B, (int64_t)h->sms * per_sm);
     *P = p;
     return NN_OK;
@@ -310,7 +319,7 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
         return NN_ERR_CUDA;
     }
     prof_mark(h, 4, s);
-    if (launch_bucket(bp, p.bucket_grid, bucket_threads(), p.bucket_smem, s) != cudaSuccess)
+    if (launch_bucket(bp, p.bucket_grid, p.bucket_threads, p.bucket_smem, s) != cudaSuccess)
         return NN_ERR_CUDA;
     prof_mark(h, 5, s);
     if (h->prof) h->pending = true;
@@ -604,8 +613,24 @@ nn_status nn_plan_info(nn_handle* h, const nn_mesh* mesh, int want, int64_t* inf
     Plan p;
     nn_status st = make_plan(h, mesh, want, &p);
     if (st != NN_OK) return st;
-    const int64_t v[6] = {p.fmt.sb, p.B, p.G, p.fmt.rb, (int64_t)p.ws_min, p.bucket_grid};
-    for (int i = 0; i < n && i < 6; ++i) info[i] = v[i];
+    const int64_t v[9] = {p.fmt.sb, p.B, p.G, p.fmt.rb, (int64_t)p.ws_min, p.bucket_grid, p.bucket_threads,
+                          (int64_t)p.bucket_smem, p.fmt.cshift};
+    for (int i = 0; i < n && i < 9; ++i) info[i] = v[i];
+    return NN_OK;
+}
+
+nn_status nn_set_tuning(nn_handle* h, const nn_tuning* t) {
+    if (!h) return NN_ERR_ARG;
+    if (!t) {
+        h->tuning = nn_tuning{};
+        return NN_OK;
+    }
+    if ((t->sb != 0 && (t->sb < SB_MIN || t->sb > SB_MAX)) ||
+        (t->bucket_threads != 0 && t->bucket_threads != 256 && t->bucket_threads != 512) ||
+        t->bucket_ctas_per_sm < 0 || t->bucket_ctas_per_sm > 4 ||
+        (t->bucket_threads == 512 && t->bucket_ctas_per_sm > 2))
+        return NN_ERR_ARG;
+    h->tuning = *t;
     return NN_OK;
 }
 

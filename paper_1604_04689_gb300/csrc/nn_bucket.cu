@@ -22,7 +22,7 @@ namespace nn {
 
 namespace {
 
-constexpr int BUCKET_THREADS = 512;
+constexpr int BUCKET_THREADS = 512;  // default block size (256 is the other choice)
 constexpr int LONG_ROW = 48;  // rows longer than this are sorted by the whole block
 constexpr int UNROLL = 2;     // records loaded per thread before they are used
 constexpr uint32_t RANK_MAX = 64;  // rows up to this length are sorted by ranking
@@ -72,8 +72,8 @@ struct BucketOut {
     int32_t* status;
 };
 
-template <int RB, int K>
-__global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
+template <int RB, int K, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_bucket(BucketParams p) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ BucketOut sh_out;
     const bool batched = p.batch.hdr != nullptr;
@@ -383,13 +383,33 @@ __global__ void __launch_bounds__(BUCKET_THREADS, 2) k_bucket(BucketParams p) {
 
 // Allow up to `bytes` of dynamic shared memory, less the kernel's own static
 // shared memory (the sum may not exceed the per-block opt-in limit).
-template <int RB, int K>
+template <int RB, int K, int THREADS>
 cudaError_t set_attr(size_t bytes) {
     cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, k_bucket<RB, K>);
+    cudaError_t e = cudaFuncGetAttributes(&a, k_bucket<RB, K, THREADS>);
     if (e != cudaSuccess) return e;
     const size_t dyn = bytes > a.sharedSizeBytes ? bytes - a.sharedSizeBytes : 0;
-    return cudaFuncSetAttribute(k_bucket<RB, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    return cudaFuncSetAttribute(k_bucket<RB, K, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
+template <int THREADS>
+void launch_t(const BucketParams& p, int grid, size_t smem, cudaStream_t s) {
+    if (p.fmt.rb == 8) {
+        if (p.fmt.k == 2) k_bucket<8, 2, THREADS><<<grid, THREADS, smem, s>>>(p);
+        else k_bucket<8, 3, THREADS><<<grid, THREADS, smem, s>>>(p);
+    } else {
+        if (p.fmt.k == 2) k_bucket<16, 2, THREADS><<<grid, THREADS, smem, s>>>(p);
+        else k_bucket<16, 3, THREADS><<<grid, THREADS, smem, s>>>(p);
+    }
+}
+
+template <int THREADS>
+cudaError_t set_attrs(size_t bytes) {
+    cudaError_t e = set_attr<8, 2, THREADS>(bytes);
+    if (e == cudaSuccess) e = set_attr<8, 3, THREADS>(bytes);
+    if (e == cudaSuccess) e = set_attr<16, 2, THREADS>(bytes);
+    if (e == cudaSuccess) e = set_attr<16, 3, THREADS>(bytes);
+    return e;
 }
 
 }  // namespace
@@ -398,26 +418,20 @@ int bucket_threads() { return BUCKET_THREADS; }
 
 cudaError_t launch_bucket(const BucketParams& p, int grid, int threads, size_t smem, cudaStream_t s) {
     if (grid <= 0) return cudaSuccess;
-    if (p.fmt.rb == 8) {
-        if (p.fmt.k == 2) k_bucket<8, 2><<<grid, threads, smem, s>>>(p);
-        else k_bucket<8, 3><<<grid, threads, smem, s>>>(p);
-    } else {
-        if (p.fmt.k == 2) k_bucket<16, 2><<<grid, threads, smem, s>>>(p);
-        else k_bucket<16, 3><<<grid, threads, smem, s>>>(p);
-    }
+    if (threads == 256) launch_t<256>(p, grid, smem, s);
+    else launch_t<512>(p, grid, smem, s);
     return cudaGetLastError();
 }
 
 cudaError_t set_bucket_smem_all(size_t bytes) {
-    cudaError_t e = set_attr<8, 2>(bytes);
-    if (e == cudaSuccess) e = set_attr<8, 3>(bytes);
-    if (e == cudaSuccess) e = set_attr<16, 2>(bytes);
-    if (e == cudaSuccess) e = set_attr<16, 3>(bytes);
+    cudaError_t e = set_attrs<512>(bytes);
+    if (e == cudaSuccess) e = set_attrs<256>(bytes);
     return e;
 }
 
 cudaError_t bucket_occupancy(int* blocks, int threads, size_t smem) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_bucket<16, 3>, threads, smem);
+    if (threads == 256) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_bucket<16, 3, 256>, 256, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_bucket<16, 3, 512>, 512, smem);
 }
 
 }  // namespace nn

@@ -45,6 +45,10 @@ class NNBatchCaps(C.Structure):
                 ("max_nodes", C.c_int64), ("max_conn", C.c_int64), ("sb", C.c_int32)]
 
 
+class NNTuning(C.Structure):
+    _fields_ = [("sb", C.c_int32), ("bucket_threads", C.c_int32), ("bucket_ctas_per_sm", C.c_int32)]
+
+
 class NNError(RuntimeError):
     def __init__(self, code: int, where: str = ""):
         self.code = code
@@ -82,6 +86,8 @@ def lib():
             L.nn_profile_enable.restype = C.c_int
             L.nn_profile_read.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]
             L.nn_profile_read.restype = C.c_int
+            L.nn_set_tuning.argtypes = [P, C.POINTER(NNTuning)]
+            L.nn_set_tuning.restype = C.c_int
             L.nn_plan_info.argtypes = [P, C.POINTER(NNMesh), C.c_int, C.POINTER(C.c_int64), C.c_int]
             L.nn_plan_info.restype = C.c_int
             L.nn_neighbors_both_noalloc.argtypes = [C.POINTER(NNMesh), C.POINTER(NNCSR), C.POINTER(NNCSR), P, P]
@@ -125,12 +131,25 @@ def nn_query(h: int, mesh: NNMesh, want: int):
     return ws.value, nc.value, ec.value
 
 
-PLAN_KEYS = ("sb", "n_buckets", "emit_ctas", "record_bytes", "ws_min", "bucket_ctas")
+PLAN_KEYS = ("sb", "n_buckets", "emit_ctas", "record_bytes", "ws_min", "bucket_ctas", "bucket_threads",
+             "bucket_smem", "partition")
+
+
+def nn_set_tuning(h: int, tuning: Optional[dict]) -> None:
+    """Apply launch tuning {'sb', 'bucket_threads', 'bucket_ctas_per_sm'} (0 = automatic); None resets."""
+    if tuning is None:
+        st = lib().nn_set_tuning(h, None)
+    else:
+        t = NNTuning(int(tuning.get("sb", 0)), int(tuning.get("bucket_threads", 0)),
+                     int(tuning.get("bucket_ctas_per_sm", 0)))
+        st = lib().nn_set_tuning(h, C.byref(t))
+    if st:
+        raise NNError(st, "nn_set_tuning")
 
 
 def nn_plan_info(h: int, mesh: NNMesh, want: int) -> dict:
-    info = (C.c_int64 * 6)()
-    st = lib().nn_plan_info(h, C.byref(mesh), want, info, 6)
+    info = (C.c_int64 * 9)()
+    st = lib().nn_plan_info(h, C.byref(mesh), want, info, 9)
     if st:
         raise NNError(st, "nn_plan_info")
     return dict(zip(PLAN_KEYS, list(info)))
