@@ -109,9 +109,9 @@ nn_status nn_query(nn_handle* h, const nn_mesh* mesh, int want, size_t* ws_bytes
 
 /* Launch tuning held by a handle, applied to its later calls (0 = the
  * library's automatic choice).  sb: log2 of the bucket width in nodes (4..11);
- * bucket_threads: 256 or 512 threads per bucket CTA; bucket_ctas_per_sm: 1, 2
- * or 4 bucket CTAs sharing an SM (sets the shared memory per CTA; 4 needs 256
- * threads).  Results never depend on tuning, only speed and workspace size.
+ * bucket_threads: 128 or 256 threads per bucket CTA; bucket_ctas_per_sm: 1..8
+ * bucket CTAs sharing an SM (sets the shared memory per CTA, which caps the
+ * bucket width).  Results never depend on tuning, only speed and workspace size.
  * nn_set_tuning(h, NULL) restores the automatic choice. */
 typedef struct {
     int32_t sb;

@@ -17,7 +17,7 @@ from typing import Optional
 from . import nn
 
 # (threads per bucket CTA, bucket CTAs per SM)
-SHAPES = ((512, 1), (512, 2), (256, 2), (256, 4))
+SHAPES = ((256, 1), (256, 2), (128, 2), (128, 4), (128, 6))
 SB_DELTAS = (-1, 0, 1)
 
 

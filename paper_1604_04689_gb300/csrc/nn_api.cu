@@ -11,8 +11,6 @@
 namespace nn {
 cudaError_t set_emit_smem_all(size_t bytes);
 cudaError_t set_bucket_smem_all(size_t bytes);
-cudaError_t bucket_occupancy(int* blocks, int threads, size_t smem);
-int bucket_threads();
 }  // namespace nn
 
 struct nn_handle {
@@ -39,8 +37,6 @@ using namespace nn;
 
 constexpr size_t ALIGN = 256;
 constexpr int SB_MIN = 4, SB_MAX = 11;
-constexpr size_t BUCKET_FIXED_PER_NODE = 28;  // bytes of per-node arrays in the bucket kernel
-constexpr size_t BUCKET_FIXED = 34 * 8 + 8 * 8;
 
 size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 int bits_for(uint64_t x) {  // bits needed to hold values 0..x (>= 1)
@@ -64,7 +60,8 @@ struct Plan {
            off_ctrl = 0, off_spill = 0, zero_begin = 0, zero_end = 0;
     size_t ws_min = 0, ws_rec = 0;
     int bucket_grid = 0;
-    int bucket_threads = 512;
+    int bucket_threads = 256;
+    int wide = 0;
     size_t bucket_smem = 0;
     uint32_t area_words = 0;
 };
@@ -95,46 +92,40 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     p.n_conn = m->n_conn;
     p.k = (m->type == NN_TRI || m->type == NN_QUAD) ? 2 : 3;
 
-    // bucket width: as many nodes as fit the bucket kernel's shared memory
-    // with room to spare for nodes of higher than average valence
+    // bucket kernel shape.  Every node goes to one lane, which holds up to
+    // 16 (or, "wide", 32) records and a 16 (32) slot neighbour table in
+    // registers; meshes whose nodes have more than ten incidences on average
+    // (tets, mixed) take the wide form with 128-thread CTAs, four per SM,
+    // the others 256-thread CTAs, two per SM.  The bucket width is then as
+    // many nodes as fit the CTA's shared memory with room to spare for nodes
+    // of higher than average valence.
     const double inc = p.N > 0 ? (double)p.n_conn / (double)p.N : 0.0;
-    const double E = (want & NN_WANT_ELEMS) ? inc : 0.0;
-    const double C = (want & NN_WANT_NODES) ? p.k * inc : 0.0;
-    const double Tt = C > 0 ? C + 1.0 : 0.0;
-    const double per_node = 4.0 * (E + 2.0 * Tt);  // element list + hash table + distinct list, bytes
-    // prefer a shared-memory size that lets two bucket CTAs share an SM, so one
-    // CTA's barriers and lookback waits overlap the other's memory traffic
-    // (many buckets are fine: the histogram pass counts them in chunks that fit
-    // its shared memory; the hard cap below only bounds workspace tables)
+    p.wide = inc > 10.0 ? 1 : 0;
+    const int ucap = p.wide ? 24 : 12;  // distinct neighbours a lane's table takes
+    p.bucket_threads = h->tuning.bucket_threads ? h->tuning.bucket_threads : (p.wide ? 128 : 256);
+    const int bcps = h->tuning.bucket_ctas_per_sm ? h->tuning.bucket_ctas_per_sm : (p.bucket_threads == 128 ? 4 : 2);
+    size_t bsmem = std::min(h->bucket_smem, h->smem_per_sm / (size_t)bcps - 2048);
+    const double U = (want & NN_WANT_NODES) ? std::min(p.k * inc / 2.0, (double)ucap) : 0.0;
+    const double per_node = 4.0 * (inc + ((want & NN_WANT_ELEMS) ? inc : 0.0) + U);  // groups, elements, neighbours
+    // (many buckets are fine: the histogram pass counts them in chunks that
+    // fit its shared memory; the hard cap below only bounds workspace tables)
     const int64_t B_lim = (int64_t)1 << 20;
+    auto fixed_of = [&](int s) { return bucket_fixed_bytes(s, p.bucket_threads, p.wide); };
     int sb = -1;
-    const int tcps = h->tuning.bucket_ctas_per_sm;  // tuned: that many bucket CTAs share an SM
-    size_t bsmem = tcps > 0 ? std::min(h->bucket_smem, h->smem_per_sm / (size_t)tcps - 2048)
-                           : std::min(h->bucket_smem, h->smem_per_sm / 2 - 2048);
-    for (int pass = 0; pass < 2 && sb < 0; ++pass) {
-        if (pass == 1) {
-            if (tcps > 0) break;
-            bsmem = h->bucket_smem;
-        }
-        for (int s = SB_MAX; s >= SB_MIN + 2; --s) {
-            if (((p.N + (1ll << s) - 1) >> s) > B_lim) break;
-            const double area = (double)bsmem - (double)BUCKET_FIXED_PER_NODE * (1 << s) - BUCKET_FIXED;
-            if (area > 0 && (double)(1 << s) * per_node <= 0.8 * area) {
-                sb = s;
-                break;
-            }
+    for (int s = SB_MAX; s >= SB_MIN; --s) {
+        if (((p.N + (1ll << s) - 1) >> s) > B_lim) break;
+        const double area = (double)bsmem - (double)fixed_of(s);
+        if (area > 0 && (double)(1 << s) * per_node <= 0.8 * area) {
+            sb = s;
+            break;
         }
     }
     if (sb < 0) sb = SB_MIN;
     if (h->tuning.sb >= SB_MIN && h->tuning.sb <= SB_MAX) sb = h->tuning.sb;
-    if (h->sb_override >= SB_MIN && h->sb_override <= SB_MAX) {
-        sb = h->sb_override;
-        bsmem = h->bucket_smem;
-    }
+    if (h->sb_override >= SB_MIN && h->sb_override <= SB_MAX) sb = h->sb_override;
+    const size_t min_area = 1024 * 4;
+    while (fixed_of(sb) + min_area > bsmem && bsmem < h->bucket_smem) bsmem = h->bucket_smem;
     p.bucket_smem = bsmem;
-    // the bucket kernel's per-node arrays must leave room for its list/table area
-    auto fixed_of = [](int s) { return BUCKET_FIXED_PER_NODE * ((size_t)1 << s) + BUCKET_FIXED; };
-    const size_t min_area = 4096 * 4;
     while (sb > SB_MIN && fixed_of(sb) + min_area > p.bucket_smem) --sb;
     const int64_t B_max = B_lim;
     auto nbk = [&](int s) { return (p.N + (1ll << s) - 1) >> s; };
@@ -194,14 +185,12 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     p.zero_end = o;
     p.off_spill = o;
     p.ws_min = o;
-    const size_t spill = (want & NN_WANT_NODES) ? ((size_t)16 << 20) + (size_t)p.n_conn * 8 : 0;
+    const size_t spill = ((size_t)16 << 20) + (size_t)p.n_conn * 8;
     p.ws_rec = o + spill;
 
-    const size_t fixed = BUCKET_FIXED_PER_NODE * ((size_t)1 << sb) + BUCKET_FIXED;
-    p.area_words = (uint32_t)((p.bucket_smem - fixed) / 4);
-    p.bucket_threads = h->tuning.bucket_threads == 256 ? 256 : bucket_threads();
+    p.area_words = (uint32_t)((p.bucket_smem - fixed_of(sb)) / 4);
     int per_sm = 1;
-    if (bucket_occupancy(&per_sm, p.bucket_threads, p.bucket_smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+    if (bucket_occupancy(&per_sm, p.bucket_threads, p.wide, p.bucket_smem) != cudaSuccess || per_sm < 1) per_sm = 1;
     p.bucket_grid = (int)std::min<int64_t>(p.B, (int64_t)h->sms * per_sm);
     *P = p;
     return NN_OK;
@@ -307,6 +296,7 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
     }
     bp.status = d_status;
     bp.area_words = p.area_words;
+    bp.wide = p.wide;
 
     prof_mark(h, 1, s);
     if (launch_hist(ep, p.emit_smem, s) != cudaSuccess) return NN_ERR_CUDA;
@@ -336,7 +326,7 @@ struct BatchPlan {
            off_lb_e = 0, off_ctrl = 0, off_spill = 0, ws_min = 0, ws_rec = 0;
     size_t bucket_smem = 0;
     uint32_t area_words = 0;
-    int bucket_grid = 0, emit_grid = 0;
+    int bucket_grid = 0, emit_grid = 0, bucket_threads = 128;
     int64_t tiles_cap = 0;
 };
 
@@ -367,14 +357,16 @@ nn_status batch_plan(const nn_handle* h, const nn_batch_caps* c, BatchPlan* out)
     p.off_spill = o;
     p.ws_min = o;
     p.ws_rec = o + (((size_t)16 << 20) + (size_t)c->max_conn * 8);
-    // shared memory: two CTAs per SM for narrow buckets, else one
-    const size_t fixed = BUCKET_FIXED_PER_NODE * ((size_t)1 << p.sb) + BUCKET_FIXED;
-    p.bucket_smem = p.sb <= 7 ? std::min(h->bucket_smem, h->smem_per_sm / 2 - 2048) : h->bucket_smem;
-    if (fixed + 4096 * 4 > p.bucket_smem) p.bucket_smem = h->bucket_smem;
+    // bucket kernel: wide lanes (a batch may hold any element type), 128
+    // threads, four CTAs per SM while the bucket fits
+    p.bucket_threads = 128;
+    const size_t fixed = bucket_fixed_bytes(p.sb, p.bucket_threads, 1);
+    p.bucket_smem = std::min(h->bucket_smem, h->smem_per_sm / 4 - 2048);
+    if (fixed + 8192 * 4 > p.bucket_smem) p.bucket_smem = h->bucket_smem;
     if (fixed + 4096 * 4 > p.bucket_smem) return NN_ERR_ARG;
     p.area_words = (uint32_t)((p.bucket_smem - fixed) / 4);
     int per_sm = 1;
-    if (bucket_occupancy(&per_sm, bucket_threads(), p.bucket_smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+    if (bucket_occupancy(&per_sm, p.bucket_threads, 1, p.bucket_smem) != cudaSuccess || per_sm < 1) per_sm = 1;
     p.bucket_grid = h->sms * per_sm;
     p.emit_grid = h->sms * (2048 / batch_threads());
     *out = p;
@@ -508,7 +500,8 @@ nn_status batch_launch(nn_handle* h, const nn_batch_caps* c, const void* staging
     kp.batch_err = reinterpret_cast<const int32_t*>(ctrl + 8);
     kp.fmt.rb = 16;
     kp.fmt.k = 3;
-    if (launch_bucket(kp, bp.bucket_grid, bucket_threads(), bp.bucket_smem, s) != cudaSuccess) return NN_ERR_CUDA;
+    kp.wide = 1;
+    if (launch_bucket(kp, bp.bucket_grid, bp.bucket_threads, bp.bucket_smem, s) != cudaSuccess) return NN_ERR_CUDA;
     return NN_OK;
 }
 
@@ -626,9 +619,8 @@ nn_status nn_set_tuning(nn_handle* h, const nn_tuning* t) {
         return NN_OK;
     }
     if ((t->sb != 0 && (t->sb < SB_MIN || t->sb > SB_MAX)) ||
-        (t->bucket_threads != 0 && t->bucket_threads != 256 && t->bucket_threads != 512) ||
-        t->bucket_ctas_per_sm < 0 || t->bucket_ctas_per_sm > 4 ||
-        (t->bucket_threads == 512 && t->bucket_ctas_per_sm > 2))
+        (t->bucket_threads != 0 && t->bucket_threads != 128 && t->bucket_threads != 256) ||
+        t->bucket_ctas_per_sm < 0 || t->bucket_ctas_per_sm > 8)
         return NN_ERR_ARG;
     h->tuning = *t;
     return NN_OK;

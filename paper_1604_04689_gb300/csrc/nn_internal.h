@@ -123,7 +123,8 @@ struct BucketParams {
     int64_t* rp_n; int32_t* col_n; int64_t cap_n;
     int64_t* rp_e; int32_t* col_e; int64_t cap_e;
     int32_t* status;
-    uint32_t area_words;    // shared-memory words available for tables and lists
+    uint32_t area_words;    // shared-memory words available for record groups and rows
+    int32_t wide;           // 1: 32 records and a 32-slot table per node in registers, 0: 16 and 16
     BatchTables batch;      // batch.hdr != nullptr: format, bucket count and meshes come from the tables
     const int32_t* batch_err;  // batches: status of the shared offsets scan, copied to every mesh
 };
@@ -139,6 +140,8 @@ cudaError_t launch_part(const EmitParams& p, cudaStream_t s);
 cudaError_t launch_part_sorted(const EmitParams& p, const uint32_t* bstart, int grid_fine, cudaStream_t s);
 cudaError_t launch_offsets(const OffsetsParams& p, cudaStream_t s);
 cudaError_t launch_bucket(const BucketParams& p, int grid, int threads, size_t smem, cudaStream_t s);
+size_t bucket_fixed_bytes(int sb, int threads, int wide);  // shared memory of the bucket kernel outside its area
+cudaError_t bucket_occupancy(int* blocks, int threads, int wide, size_t smem);
 cudaError_t launch_batch_emit(const BatchTables& bt, uint32_t* bcount, uint32_t* gcur, uint8_t* rec,
                               uint64_t* lb_off, uint64_t* lb_n, uint64_t* lb_e, uint32_t* ctrl, int grid,
                               int stage, cudaStream_t s);

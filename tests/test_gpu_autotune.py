@@ -70,8 +70,8 @@ def test_tuned_caches_and_reapplies(tmp_path):
 
 def test_invalid_tunings_rejected():
     b = nn.Builder()
-    for t in ({"sb": 3}, {"sb": 12}, {"bucket_threads": 128}, {"bucket_ctas_per_sm": 5},
-              {"bucket_threads": 512, "bucket_ctas_per_sm": 4}):
+    for t in ({"sb": 3}, {"sb": 12}, {"bucket_threads": 512}, {"bucket_threads": 64}, {"bucket_ctas_per_sm": 9},
+              {"bucket_ctas_per_sm": -1}):
         with pytest.raises(nn.NNError):
             nn.nn_set_tuning(b.h, t)
     nn.nn_set_tuning(b.h, None)
