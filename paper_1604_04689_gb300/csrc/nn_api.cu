@@ -56,6 +56,8 @@ struct Plan {
     int G_part = 1;
     int G_fine = 1;
     size_t emit_smem = 0;
+    size_t off_estart = 0, off_nfc = 0, outbox_bytes = 0;
+    uint32_t outbox_words = 0;
     size_t off_hist = 0, off_bstart = 0, off_gcur = 0, off_gcur_c = 0, off_rec_tmp = 0, off_rec = 0, off_lb_off = 0, off_lb_n = 0, off_lb_e = 0,
            off_ctrl = 0, off_spill = 0, zero_begin = 0, zero_end = 0;
     size_t ws_min = 0, ws_rec = 0;
@@ -169,15 +171,22 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
         p.G_part = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sms * 4, (n_units + 511) / 512));
     p.G_fine = h->sms * 4;
 
+    p.area_words = (uint32_t)((p.bucket_smem - fixed_of(sb)) / 4);
+    int per_sm = 1;
+    if (bucket_occupancy(&per_sm, p.bucket_threads, p.wide, p.bucket_smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+    p.bucket_grid = (int)std::min<int64_t>(p.B, (int64_t)h->sms * per_sm);
+
     // workspace layout
     size_t o = 0;
     p.off_hist = o; o = align_up(o + (size_t)p.G * p.B * 4);
     p.off_bstart = o; o = align_up(o + ((size_t)p.B + 1) * 4);
+    p.off_estart = o; o = align_up(o + ((want & NN_WANT_ELEMS) ? ((size_t)p.B + 1) * 4 : 0));
     p.off_gcur = o; o = align_up(o + (size_t)p.B * 4);
     p.off_gcur_c = o; o = align_up(o + 256 * 4);
     p.off_rec_tmp = o; o = align_up(o + (f.cshift > 0 ? (size_t)p.n_conn * f.rb : 0));
     p.off_rec = o; o = align_up(o + (size_t)p.n_conn * f.rb);
     p.zero_begin = o;
+    p.off_nfc = o; o = align_up(o + ((want & NN_WANT_ELEMS) ? (size_t)p.B * 4 : 0));
     p.off_lb_off = o; o = align_up(o + (size_t)((p.B + OFFSETS_THREADS - 1) / OFFSETS_THREADS) * 8 + 8);
     p.off_lb_n = o; o = align_up(o + ((want & NN_WANT_NODES) ? (size_t)p.B * 8 : 0));
     p.off_lb_e = o; o = align_up(o + ((want & NN_WANT_ELEMS) ? (size_t)p.B * 8 : 0));
@@ -186,12 +195,15 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     p.off_spill = o;
     p.ws_min = o;
     const size_t spill = ((size_t)16 << 20) + (size_t)p.n_conn * 8;
-    p.ws_rec = o + spill;
+    // bucket CTAs' outboxes (node offsets and rows of a bucket awaiting its
+    // offset; room for a little more than the average distinct-neighbour
+    // count per node, a bucket with more writes its rows without parking
+    // them), at the end of the workspace when it has room beside the spill
+    // area; without them every bucket writes its rows as soon as it can
+    p.outbox_words = (want & NN_WANT_NODES) ? std::min<uint32_t>(p.area_words, (uint32_t)(p.wide ? 20 : 10) << sb) : 0;
+    p.outbox_bytes = p.outbox_words ? align_up((size_t)p.bucket_grid * (((size_t)1 << sb) + p.outbox_words) * 4) : 0;
+    p.ws_rec = o + spill + p.outbox_bytes;
 
-    p.area_words = (uint32_t)((p.bucket_smem - fixed_of(sb)) / 4);
-    int per_sm = 1;
-    if (bucket_occupancy(&per_sm, p.bucket_threads, p.wide, p.bucket_smem) != cudaSuccess || per_sm < 1) per_sm = 1;
-    p.bucket_grid = (int)std::min<int64_t>(p.B, (int64_t)h->sms * per_sm);
     *P = p;
     return NN_OK;
 }
@@ -252,6 +264,7 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
     ep.n_cta = p.G;
     ep.n_cta_part = p.G_part;
     ep.hist = reinterpret_cast<uint32_t*>(w + p.off_hist);
+    ep.nfc = (want & NN_WANT_ELEMS) ? reinterpret_cast<uint32_t*>(w + p.off_nfc) : nullptr;
     ep.gcur = reinterpret_cast<uint32_t*>(w + p.off_gcur);
     ep.gcur_coarse = reinterpret_cast<uint32_t*>(w + p.off_gcur_c);
     ep.rec_tmp = w + p.off_rec_tmp;
@@ -264,6 +277,8 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
     op.n_cta = p.G;
     op.n_buckets = p.B;
     op.bstart = reinterpret_cast<uint32_t*>(w + p.off_bstart);
+    op.nfc = ep.nfc;
+    op.estart = (want & NN_WANT_ELEMS) ? reinterpret_cast<uint32_t*>(w + p.off_estart) : nullptr;
     op.gcur = ep.gcur;
     op.gcur_coarse = ep.gcur_coarse;
     op.cshift = p.fmt.cshift;
@@ -278,12 +293,20 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
     bp.n_buckets = p.B;
     bp.rec = ep.rec;
     bp.bstart = op.bstart;
+    bp.estart = op.estart;
     bp.lb_n = reinterpret_cast<uint64_t*>(w + p.off_lb_n);
     bp.lb_e = reinterpret_cast<uint64_t*>(w + p.off_lb_e);
     bp.ticket = ctrl + 1;
     bp.spill_cursor = reinterpret_cast<unsigned long long*>(ctrl + 2);
     bp.spill = reinterpret_cast<uint32_t*>(w + p.off_spill);
-    bp.spill_words = ws_bytes > p.off_spill ? (ws_bytes - p.off_spill) / 4 : 0;
+    size_t spill_bytes = ws_bytes > p.off_spill ? ws_bytes - p.off_spill : 0;
+    if (p.outbox_bytes && spill_bytes >= p.outbox_bytes + ((size_t)16 << 20)) {
+        const size_t ob = (ws_bytes - p.outbox_bytes) & ~(ALIGN - 1);
+        bp.outbox = reinterpret_cast<uint32_t*>(w + ob);
+        bp.outbox_words = p.outbox_words;
+        spill_bytes = ob - p.off_spill;
+    }
+    bp.spill_words = spill_bytes / 4;
     if (want & NN_WANT_NODES) {
         bp.rp_n = nodes->row_ptr;
         bp.col_n = nodes->col;
@@ -323,9 +346,9 @@ struct BatchPlan {
     int64_t B_cap = 0;
     size_t hdr_bytes = 0, meshes_off = 0, elem_off_off = 0, bucket_off_off = 0, table_bytes = 0;
     size_t off_bcount = 0, off_bstart = 0, off_gcur = 0, off_rec = 0, off_lb_off = 0, off_lb_n = 0,
-           off_lb_e = 0, off_ctrl = 0, off_spill = 0, ws_min = 0, ws_rec = 0;
+           off_lb_e = 0, off_ctrl = 0, off_spill = 0, ws_min = 0, ws_rec = 0, outbox_bytes = 0;
     size_t bucket_smem = 0;
-    uint32_t area_words = 0;
+    uint32_t area_words = 0, outbox_words = 0;
     int bucket_grid = 0, emit_grid = 0, bucket_threads = 128;
     int64_t tiles_cap = 0;
 };
@@ -344,19 +367,6 @@ nn_status batch_plan(const nn_handle* h, const nn_batch_caps* c, BatchPlan* out)
     p.elem_off_off = p.meshes_off + align_up((size_t)c->max_meshes * sizeof(BatchMesh));
     p.bucket_off_off = p.elem_off_off + align_up(((size_t)c->max_meshes + 1) * 8);
     p.table_bytes = p.bucket_off_off + align_up(((size_t)c->max_meshes + 1) * 8);
-    size_t o = p.table_bytes;
-    p.off_bcount = o; o = align_up(o + (size_t)p.B_cap * 4);
-    p.off_bstart = o; o = align_up(o + ((size_t)p.B_cap + 1) * 4);
-    p.off_gcur = o; o = align_up(o + (size_t)p.B_cap * 4);
-    p.off_rec = o; o = align_up(o + (size_t)c->max_conn * 16);
-    p.tiles_cap = (p.B_cap + OFFSETS_THREADS - 1) / OFFSETS_THREADS;
-    p.off_lb_off = o; o = align_up(o + ((size_t)p.tiles_cap + 1) * 8);
-    p.off_lb_n = o; o = align_up(o + (size_t)p.B_cap * 8);
-    p.off_lb_e = o; o = align_up(o + (size_t)p.B_cap * 8);
-    p.off_ctrl = o; o = align_up(o + 64);
-    p.off_spill = o;
-    p.ws_min = o;
-    p.ws_rec = o + (((size_t)16 << 20) + (size_t)c->max_conn * 8);
     // bucket kernel: wide lanes (a batch may hold any element type), 128
     // threads, four CTAs per SM while the bucket fits
     p.bucket_threads = 128;
@@ -368,6 +378,21 @@ nn_status batch_plan(const nn_handle* h, const nn_batch_caps* c, BatchPlan* out)
     int per_sm = 1;
     if (bucket_occupancy(&per_sm, p.bucket_threads, 1, p.bucket_smem) != cudaSuccess || per_sm < 1) per_sm = 1;
     p.bucket_grid = h->sms * per_sm;
+    size_t o = p.table_bytes;
+    p.off_bcount = o; o = align_up(o + (size_t)p.B_cap * 4);
+    p.off_bstart = o; o = align_up(o + ((size_t)p.B_cap + 1) * 4);
+    p.off_gcur = o; o = align_up(o + (size_t)p.B_cap * 4);
+    p.off_rec = o; o = align_up(o + (size_t)c->max_conn * 16);
+    p.tiles_cap = (p.B_cap + OFFSETS_THREADS - 1) / OFFSETS_THREADS;
+    p.off_lb_off = o; o = align_up(o + ((size_t)p.tiles_cap + 1) * 8);
+    p.off_lb_n = o; o = align_up(o + (size_t)p.B_cap * 8);
+    p.off_lb_e = o; o = align_up(o + (size_t)p.B_cap * 8);
+    p.off_ctrl = o; o = align_up(o + 64);
+    p.outbox_words = std::min<uint32_t>(p.area_words, 20u << p.sb);
+    p.off_spill = o;
+    p.ws_min = o;
+    p.outbox_bytes = align_up((size_t)p.bucket_grid * (((size_t)1 << p.sb) + p.outbox_words) * 4);
+    p.ws_rec = o + (((size_t)16 << 20) + (size_t)c->max_conn * 8) + p.outbox_bytes;
     p.emit_grid = h->sms * (2048 / batch_threads());
     *out = p;
     return NN_OK;
@@ -494,7 +519,14 @@ nn_status batch_launch(nn_handle* h, const nn_batch_caps* c, const void* staging
     kp.ticket = ctrl + 1;
     kp.spill_cursor = reinterpret_cast<unsigned long long*>(ctrl + 2);
     kp.spill = reinterpret_cast<uint32_t*>(w + bp.off_spill);
-    kp.spill_words = ws_bytes > bp.off_spill ? (ws_bytes - bp.off_spill) / 4 : 0;
+    size_t spill_bytes = ws_bytes > bp.off_spill ? ws_bytes - bp.off_spill : 0;
+    if (spill_bytes >= bp.outbox_bytes + ((size_t)16 << 20)) {
+        const size_t ob = (ws_bytes - bp.outbox_bytes) & ~(ALIGN - 1);
+        kp.outbox = reinterpret_cast<uint32_t*>(w + ob);
+        kp.outbox_words = bp.outbox_words;
+        spill_bytes = ob - bp.off_spill;
+    }
+    kp.spill_words = spill_bytes / 4;
     kp.area_words = bp.area_words;
     kp.batch = bt;
     kp.batch_err = reinterpret_cast<const int32_t*>(ctrl + 8);

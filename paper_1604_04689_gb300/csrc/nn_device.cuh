@@ -123,6 +123,64 @@ __device__ inline uint64_t lb_resolve(uint64_t* state, uint64_t t, uint64_t agg,
     return excl;
 }
 
+// As lb_resolve, but every lane reads V consecutive predecessors per step
+// (32 V per step): when hundreds of tiles are in flight, the nearest
+// inclusive prefix is that far back, and each step is an L2 round trip.
+template <int V>
+__device__ inline uint64_t lb_resolve_wide(uint64_t* state, uint64_t t, uint64_t agg, int32_t* status,
+                                           uint64_t first = 0) {
+    const int lane = threadIdx.x & 31;
+    if (t == first) return 0;
+    uint64_t excl = 0;
+    int64_t p = (int64_t)t - 1;  // nearest predecessor not yet consumed
+    uint64_t t0 = 0;
+    for (;;) {
+        uint64_t s[V];
+        int nr = V, inc = V;  // first not-ready / first inclusive among this lane's V (nearest first)
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const int64_t idx = p - (int64_t)lane * V - j;
+            s[j] = idx >= (int64_t)first ? ld_acquire(&state[idx]) : LB_INC;  // before the chain: zero
+        }
+#pragma unroll
+        for (int j = V - 1; j >= 0; --j) {
+            if ((s[j] >> 62) == 0) nr = j;
+            if ((s[j] >> 62) == 2) inc = j;
+        }
+        const unsigned nr_lanes = __ballot_sync(0xffffffffu, nr < V);
+        const unsigned inc_lanes = __ballot_sync(0xffffffffu, inc < V);
+        const int l_nr = nr_lanes ? __ffs(nr_lanes) - 1 : 32, l_inc = inc_lanes ? __ffs(inc_lanes) - 1 : 32;
+        const int k_nr = l_nr < 32 ? l_nr * V + __shfl_sync(0xffffffffu, nr, l_nr & 31) : 32 * V;
+        const int k_inc = l_inc < 32 ? l_inc * V + __shfl_sync(0xffffffffu, inc, l_inc & 31) : 32 * V;
+        const bool done = k_inc < k_nr;  // an inclusive prefix before any gap: consume through it
+        const int lim = done ? k_inc + 1 : k_nr;
+        uint64_t v = 0;
+#pragma unroll
+        for (int j = 0; j < V; ++j)
+            if (lane * V + j < lim) v += s[j] & LB_VAL;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+        excl += v;
+        if (done) break;
+        p -= k_nr;
+        if (k_nr == 0) {  // nearest predecessor not ready yet: bounded wait
+            const uint64_t now = global_ns();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > WAIT_LIMIT_NS) {
+                if (lane == 0) set_status(status, NN_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(100);
+        } else {
+            t0 = 0;
+        }
+    }
+    if (lane == 0) st_release(&state[t], LB_INC | ((excl + agg) & LB_VAL));
+    __syncwarp();
+    return excl;
+}
+
 __device__ inline uint64_t warp_lookback(uint64_t* state, uint64_t t, uint64_t agg, int32_t* status) {
     if ((threadIdx.x & 31) == 0) lb_publish(state, t, agg);
     __syncwarp();

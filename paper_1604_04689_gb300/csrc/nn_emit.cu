@@ -113,9 +113,10 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_hist(EmitParams p) {
         const int64_t nc = min(B - c0, p.hist_chunk);
         for (int64_t b = threadIdx.x; b < nc; b += blockDim.x) sh_hist[b] = 0;
         __syncthreads();
-        walk_cta<TYPE>(p, [&](int32_t v, int, int64_t, int32_t, int32_t, int32_t) {
+        walk_cta<TYPE>(p, [&](int32_t v, int nf, int64_t, int32_t, int32_t, int32_t) {
             const int64_t b = (int64_t)(v >> sb) - c0;
             if (b >= 0 && b < nc) atomicAdd(&sh_hist[b], 1u);
+            if (nf && c0 == 0 && p.nfc) atomicAdd(&p.nfc[v >> sb], 1u);  // rare: degenerate elements only
         });
         __syncthreads();
         for (int64_t b = threadIdx.x; b < nc; b += blockDim.x) row[c0 + b] = sh_hist[b];
@@ -528,19 +529,30 @@ __global__ void __launch_bounds__(OFFSETS_THREADS) k_offsets(OffsetsParams p) {
     const uint32_t tile = sh_tile;
     const int64_t B = p.hdr ? p.hdr->n_buckets : p.n_buckets;
     const int64_t b = (int64_t)tile * blockDim.x + threadIdx.x;
-    uint64_t tot = 0;
-    if (b < B)
+    uint64_t tot = 0, nf = 0;
+    if (b < B) {
         for (int c = 0; c < p.n_cta; ++c) tot += p.hist[(int64_t)c * B + b];
+        if (p.nfc) nf = p.nfc[b];
+    }
+    // records (low 31 bits) and repeated-node records (next 31) in one scan;
+    // both totals stay below 2^31
     uint64_t agg;
-    uint64_t ex = block_excl_scan(tot, &agg, sh_scan);
+    const uint64_t ex2 = block_excl_scan(tot | (nf << 31), &agg, sh_scan);
+    const uint64_t ex = ex2 & 0x7fffffffull, ex_nf = ex2 >> 31;
     if (threadIdx.x < 32) {
         const uint64_t base = warp_lookback(p.lb_state, tile, agg, p.status);
         if (threadIdx.x == 0) sh_base = base;
     }
     __syncthreads();
     if (b < B) {
-        const uint64_t run = sh_base + ex;
+        const uint64_t base = sh_base & 0x7fffffffull, base_nf = sh_base >> 31;
+        const uint64_t run = base + ex;
         p.bstart[b] = (uint32_t)min(run, p.rec_cap);
+        if (p.estart) {
+            const uint64_t erun = run - (base_nf + ex_nf);
+            p.estart[b] = (uint32_t)min(erun, p.rec_cap);
+            if (b == B - 1) p.estart[B] = (uint32_t)min(erun + tot - nf, p.rec_cap);
+        }
         p.gcur[b] = (uint32_t)min(run, p.rec_cap);
         if (p.cshift > 0 && (b & ((1ll << p.cshift) - 1)) == 0) p.gcur_coarse[b >> p.cshift] = (uint32_t)min(run, p.rec_cap);
         if (b == B - 1) p.bstart[B] = (uint32_t)min(run + tot, p.rec_cap);

@@ -48,6 +48,7 @@ struct EmitParams {
     int n_cta;        // CTAs of the histogram pass (rows of hist)
     int n_cta_part;   // CTAs of the partition pass
     uint32_t* hist;   // [n_cta][n_buckets] record counts of each CTA's element slice
+    uint32_t* nfc;    // [n_buckets] records of a node already seen in its element (they add no element entry)
     uint32_t* gcur;   // [n_buckets] write cursor of each bucket (starts at the bucket start)
     uint32_t* gcur_coarse;  // [256] write cursor of each coarse region (two-level partition)
     uint8_t* rec_tmp; // records grouped by coarse region (two-level partition)
@@ -63,6 +64,8 @@ struct OffsetsParams {
     int n_cta;
     int64_t n_buckets;
     uint32_t* bstart;       // [n_buckets+1] first record of each bucket
+    const uint32_t* nfc;    // [n_buckets] repeated-node records (nullptr: no element offsets)
+    uint32_t* estart;       // [n_buckets+1] first element-CSR entry of each bucket (with nfc)
     uint32_t* gcur;         // [n_buckets] set to the bucket starts
     uint32_t* gcur_coarse;  // [256] set to the coarse region starts (when cshift > 0)
     int cshift;
@@ -114,6 +117,7 @@ struct BucketParams {
     int64_t n_buckets;
     const uint8_t* rec;
     const uint32_t* bstart;
+    const uint32_t* estart; // element-CSR offset of each bucket (nullptr: found by lookback in lb_e)
     uint64_t* lb_n;         // lookback words, node CSR, one per bucket
     uint64_t* lb_e;         // lookback words, element CSR, one per bucket
     uint32_t* ticket;
@@ -124,6 +128,8 @@ struct BucketParams {
     int64_t* rp_e; int32_t* col_e; int64_t cap_e;
     int32_t* status;
     uint32_t area_words;    // shared-memory words available for record groups and rows
+    uint32_t* outbox;       // per CTA: node offsets [2^sb] then rows [outbox_words] of the bucket awaiting its offset
+    uint32_t outbox_words;
     int32_t wide;           // 1: 32 records and a 32-slot table per node in registers, 0: 16 and 16
     BatchTables batch;      // batch.hdr != nullptr: format, bucket count and meshes come from the tables
     const int32_t* batch_err;  // batches: status of the shared offsets scan, copied to every mesh

@@ -146,6 +146,22 @@ def test_degenerate_elements(builder):
         check_against_oracle(mg.Mesh(t, 45, conn.ravel()), nn.WANT_BOTH, builder)
 
 
+@pytest.mark.parametrize("sb", [None, 4])
+def test_degenerate_elements_many_buckets(sb):
+    """Repeated nodes scattered over many buckets: element-CSR offsets of every
+    bucket discount the repeated-node records of all buckets before it."""
+    rng = np.random.default_rng(12)
+    for m in (mg.tri_grid(200, 3), mg.tet_grid(25, 4), mg.hex_grid(30, 5)):
+        conn = m.conn.reshape(m.n_elems, -1).copy()
+        hit = rng.random(m.n_elems) < 0.05
+        conn[hit, 1] = conn[hit, 0]                      # collapse one edge
+        dm = mg.Mesh(m.etype, m.n_nodes, conn.ravel())
+        with env(**({"NN_SB": sb} if sb else {})):
+            b = nn.Builder()
+        check_against_oracle(dm, nn.WANT_BOTH, b, ws_extra=64 * dm.n_conn)
+        check_against_oracle(dm, nn.WANT_ELEMS, b, ws_extra=64 * dm.n_conn)
+
+
 def test_random_mixed_soup(builder):
     rng = np.random.default_rng(9)
     el = []
