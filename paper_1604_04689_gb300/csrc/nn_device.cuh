@@ -21,6 +21,14 @@ __device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
+// Relaxed load: for lookback words, which carry their flag and value in one
+// 64-bit word (nothing else is read on the strength of the flag), so several
+// can be in flight at once.
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -140,7 +148,7 @@ __device__ inline uint64_t lb_resolve_wide(uint64_t* state, uint64_t t, uint64_t
 #pragma unroll
         for (int j = 0; j < V; ++j) {
             const int64_t idx = p - (int64_t)lane * V - j;
-            s[j] = idx >= (int64_t)first ? ld_acquire(&state[idx]) : LB_INC;  // before the chain: zero
+            s[j] = idx >= (int64_t)first ? ld_relaxed(&state[idx]) : LB_INC;  // before the chain: zero
         }
 #pragma unroll
         for (int j = V - 1; j >= 0; --j) {
