@@ -35,6 +35,8 @@ WORKLOADS = {
     "tet161": ("config_mesh(2)", "Kuhn tet grid 161^3 (4,173,281 nodes, 24,576,000 tets), seed 2, permuted"),
     "hex257": ("config_mesh(3)", "hex grid 257^3 (16,974,593 nodes, 16,777,216 hexes), seed 3, node ids permuted"),
     "mixed257": ("config_mesh(3, 'mixed')", "hex grid 257^3 with 30% of cells split into 6 tets, seed 103"),
+    "tri1448": ("tri_grid(1448, 5)", "triangle grid 1448x1448 (2,096,704 nodes, 4,187,618 tris), seed 5, "
+                                     "permuted (the profiling case: records exceed L2, a few hundred MB on the device)"),
     "tri64": ("config_mesh(0)", "triangle grid 64x64 (4,096 nodes, 7,938 tris), seed 0, permuted"),
     "serve": (None, "stream of 10,000 mesh requests (tri / Kuhn tet / hex grids, elements log-uniform "
                     "1e3-2e6, per-request seeds), Poisson arrivals at 0.8x the plain saturated rate, "
