@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--impl", choices=["ours", "reference", "sortpipe"], default="ours",
+                    help="sortpipe: the paper's sort / unique-by-key pipeline on the GPU with library primitives "
+                         "(benchmark-only comparison, not part of the library)")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="tri2048")
     ap.add_argument("--want", choices=list(WANT), default="both")
     ap.add_argument("--no-baseline", action="store_true", help="skip the oracle CPU baseline")
@@ -61,6 +63,7 @@ def parse():
                     help="launch tuning: cached or timed once (auto), planner default (off), re-timed (sweep)")
     ap.add_argument("--requests", type=int, default=10000, help="serve workload: number of requests")
     ap.add_argument("--load", type=float, default=0.8, help="serve workload: arrival rate / plain saturated rate")
+    ap.add_argument("--loads", default="", help="serve workload: also sweep these comma-separated loads")
     return ap.parse_args()
 
 
@@ -144,9 +147,23 @@ def oracle_baseline(seconds_hint=20.0):
     r = oracle.neighbors(mesh, oracle.BOTH)
     dt = time.perf_counter() - t0
     assert r["status"] == 0
-    return {"value": mesh.n_elems / dt / 1e6, "unit": "Melem/s", "cores": 1, "kind": "oracle",
+    return {"value": mesh.n_elems / dt / 1e6, "unit": "Melem/s", "cores": 1, "kind": "oracle", "host": host_info(),
             "sample": f"triangle grid {n}x{n} ({mesh.n_elems} tris, seed 1, permuted), both CSRs, "
                       f"single-threaded std::set oracle, {dt:.1f} s"}
+
+
+def host_info():
+    """The host the oracle ran on: model name and core count (one core used)."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return f"{model or 'unknown CPU'}, 1 of {os.cpu_count()} cores used"
 
 
 def reference_arm(args):
@@ -173,9 +190,77 @@ def reference_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, "want": args.want, "sample": sample},
-            "cpu_baseline": {"value": v, "unit": "Melem/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "Melem/s", "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": host_info()},
             "e2e": {"value": v, "unit": "Melem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------- paper's pipeline
+
+LOCAL_EDGES = {0: ((0, 1), (1, 2), (2, 0)), 1: ((0, 1), (1, 2), (2, 3), (3, 0)),
+               2: ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)),
+               3: ((0, 1), (1, 2), (2, 3), (3, 0), (4, 5), (5, 6), (6, 7), (7, 4), (0, 4), (1, 5), (2, 6), (3, 7))}
+
+
+def sortpipe_arm(args):
+    """The paper's GPU recipe (Sec. 2.2.1) on this GPU with library primitives: every element emits its
+    directed edge pairs (both orientations) and its (node, element) pairs as 64-bit keys, a radix sort
+    orders them by key, and unique-by-key with counts gives the rows; duplicates are dropped (the set
+    reading of a one-ring).  Benchmark-only: it is the comparison the paper's design makes possible, not
+    a code path of the library.  Checked against the library's own build once, bit for bit."""
+    import torch
+    from paper_1604_04689_gb300 import nn
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    mesh = make_mesh(args.workload)
+    if mesh.etype not in LOCAL_EDGES:
+        print(json.dumps({"impl": "sortpipe", "unavailable": "uniform element types only"}))
+        return
+    N, T = mesh.n_nodes, mesh.n_elems
+    conn = torch.from_numpy(mesh.conn).to(dev).view(T, -1).to(torch.int64)
+    eid = torch.arange(T, device=dev, dtype=torch.int64)
+
+    def build():
+        a = torch.cat([conn[:, i] for i, j in LOCAL_EDGES[mesh.etype]] + [conn[:, j] for i, j in LOCAL_EDGES[mesh.etype]])
+        b = torch.cat([conn[:, j] for i, j in LOCAL_EDGES[mesh.etype]] + [conn[:, i] for i, j in LOCAL_EDGES[mesh.etype]])
+        keep = a != b
+        keys = torch.sort((a * N + b)[keep]).values
+        u = torch.unique_consecutive(keys)
+        rp_n = torch.zeros(N + 1, dtype=torch.int64, device=dev)
+        rp_n[1:] = torch.cumsum(torch.bincount(u // N, minlength=N), 0)
+        col_n = (u % N).to(torch.int32)
+        ek = torch.unique_consecutive(torch.sort((conn * T + eid[:, None]).reshape(-1)).values)
+        rp_e = torch.zeros(N + 1, dtype=torch.int64, device=dev)
+        rp_e[1:] = torch.cumsum(torch.bincount(ek // T, minlength=N), 0)
+        col_e = (ek % T).to(torch.int32)
+        return rp_n, col_n, rp_e, col_e
+
+    ref = nn.Builder(dev).build(nn.DeviceMesh.from_host(mesh, device=dev))
+    got = build()
+    match = all(torch.equal(x, y.to(x.dtype)) for x, y in
+                zip(got, (ref["nodes"][0], ref["nodes"][1], ref["elems"][0], ref["elems"][1])))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(max(args.warmup, 1)):
+        build()
+    torch.cuda.synchronize(dev)
+    stream = torch.cuda.current_stream(dev)
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        build()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(e0.elapsed_time(e1))
+    ms = sum(times) / len(times)
+    print(json.dumps({"metric": "neighbor_csr_build_throughput", "value": T / (ms * 1e-3) / 1e6, "unit": "Melem/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "dtype": "int64 keys", "data": "synthetic", "impl": "sortpipe",
+                      "config": {"workload": args.workload, "want": "both",
+                                 "pipeline": "torch.sort (radix) + unique_consecutive + bincount/cumsum"},
+                      "matches_library": bool(match)}), flush=True)
 
 
 # ---------------------------------------------------------------- ours
@@ -208,6 +293,11 @@ def serve_bench(args):
         sampler.start()
     res_p = plain.run(copy.deepcopy(trace))
     res_b = batched.run(copy.deepcopy(trace))
+    sweep = {}
+    for ld in [float(x) for x in args.loads.split(",") if x.strip()]:
+        tr = make_requests(n, ld * sat["req_per_s"])
+        sweep[str(ld)] = {"rate_req_per_s": ld * sat["req_per_s"], "plain": plain.run(copy.deepcopy(tr)),
+                          "batched": batched.run(copy.deepcopy(tr))}
     clocks = None if args.no_clocks else sampler.stop()
     line = {"metric": "neighbor_csr_build_throughput", "value": res_b["melem_per_s"], "unit": "Melem/s",
             "n_gpus": 1, "steps": n, "warmup": w, "ms_per_step": res_b["makespan_s"] * 1e3 / n,
@@ -218,7 +308,7 @@ def serve_bench(args):
                        "inputs": "generated on the device per request (stand-in for the upload)",
                        "l2": "inputs of the whole stream exceed L2"},
             "serving": {"plain_saturated": sat, "plain": res_p, "batched": res_b,
-                        "batches": batched.batches, "lanes": 2},
+                        "batches": batched.batches, "lanes": 2, "load_sweep": sweep},
             "clocks": clocks, "gpu_launches": None, "e2e": None, "cpu_baseline": None}
     print(json.dumps(line), flush=True)
 
@@ -227,6 +317,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.impl == "sortpipe":
+        sortpipe_arm(args)
         return
     if args.workload == "serve":
         serve_bench(args)
@@ -298,11 +391,9 @@ def main():
     clocks = None if args.no_clocks else sampler.stop()
     status = int(b.status.item())
     assert status == 0, nn.STATUS[status]
-    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    per_step = sorted(s.elapsed_time(e) for s, e in zip(starts, ends))
+    total_ms = sum(per_step)
+    total_ms = max_over_ranks(total_ms, world, dev)
 
     # ---- result sizes and algorithmic bytes
     nnz = {}
@@ -334,7 +425,7 @@ def main():
         except Exception:
             traffic = None
     ms_per_step = total_ms / args.steps
-    value = world * T * args.steps / (total_ms * 1e-3) / 1e6
+    value = whole_job_value(T, args.steps, world, total_ms)
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -362,6 +453,8 @@ def main():
                      "achieved_gbs": pipeline_bytes / (ms_per_step * 1e-3) / 1e9,
                      "frac": pipeline_bytes / (ms_per_step * 1e-3) / 1e9 / peak,
                      "stage_ms_per_step": {k: v / max(calls, 1) for k, v in stage_ms.items()},
+                     "step_ms_median": per_step[len(per_step) // 2],
+                     "step_ms_p95": per_step[min(len(per_step) - 1, int(0.95 * len(per_step)))],
                      "wall_s": t_wall},
         "gpu_launches": launches_per_build(plan) * args.steps,
         "clocks": clocks,
@@ -414,6 +507,23 @@ def end_to_end(torch, nn, b, mesh, dm, want, ws, ws_bytes, out, steps, dev, worl
     return {"value": world * mesh.n_elems * steps / dt / 1e6, "unit": "Melem/s",
             "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
             "ms_per_step": dt * 1e3 / steps}
+
+
+def max_over_ranks(x, world, device):
+    """The slowest rank's time: every rank contributes, all receive the maximum."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(n_elems, steps, world, total_ms):
+    """Melem/s of the whole job: every replica builds the same mesh `steps` times within the slowest
+    rank's time (weak scaling)."""
+    return world * n_elems * steps / (total_ms * 1e-3) / 1e6
 
 
 def launches_per_build(plan):

@@ -41,6 +41,7 @@ class Request:
     n_nodes: int = 0
     n_elems: int = 0
     t_done: float = -1.0
+    t_start: float = -1.0  # device time its build was enqueued behind (after its input was generated)
     status: int = -1
     result: Optional[dict] = None
 
@@ -120,6 +121,7 @@ class _Lane:
         self.graph = None
         self.use_graph = use_graph
         self.event = torch.cuda.Event(enable_timing=True)
+        self.ev_start = torch.cuda.Event(enable_timing=True)
         self.reqs = None
         self.bufs = None
 
@@ -162,13 +164,17 @@ def _alloc_and_generate(torch, r: Request, device, stream, want):
 
 def _stats(reqs: List[Request], t_first: float, t_last: float) -> dict:
     lat = np.array([r.t_done - r.arrival for r in reqs])
+    build = np.array([r.t_done - r.t_start for r in reqs if r.t_start >= 0])
     elems = sum(r.n_elems for r in reqs)
     span = max(t_last - t_first, 1e-9)
-    return {"requests": len(reqs), "elements": int(elems), "makespan_s": span,
-            "req_per_s": len(reqs) / span, "melem_per_s": elems / span / 1e6,
-            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3),
-            "failed": int(sum(1 for r in reqs if r.status != 0))}
+    out = {"requests": len(reqs), "elements": int(elems), "makespan_s": span,
+           "req_per_s": len(reqs) / span, "melem_per_s": elems / span / 1e6,
+           "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+           "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3),
+           "failed": int(sum(1 for r in reqs if r.status != 0))}
+    if build.size:  # completion minus the start of the request's build (queueing and generation excluded)
+        out.update(build_p50_ms=float(np.percentile(build, 50) * 1e3), build_p99_ms=float(np.percentile(build, 99) * 1e3))
+    return out
 
 
 class BatchServer:
@@ -207,8 +213,10 @@ class BatchServer:
                 if lane.event.query():
                     t_done = ev0.elapsed_time(lane.event) * 1e-3
                     stat = lane.bb.status[: len(lane.reqs)].cpu().tolist()
+                    t_start = ev0.elapsed_time(lane.ev_start) * 1e-3
                     for r, (dm, out), s in zip(lane.reqs, lane.bufs, stat):
                         r.t_done = t_done
+                        r.t_start = t_start
                         r.status = int(s)
                         if self.keep:
                             r.result = {k: (rp, col) for k, (rp, col) in out.items()}
@@ -229,6 +237,7 @@ class BatchServer:
                     st = lane.bb.prepare([d for d, _ in bufs], [o for _, o in bufs])
                     if st:
                         raise nn.NNError(st, "nn_batch_prepare")
+                    lane.ev_start.record(lane.stream)
                     lane.launch()
                     lane.event.record(lane.stream)
                     lane.reqs, lane.bufs = batch, bufs
@@ -276,22 +285,25 @@ class PlainServer:
         while pending or inflight:
             now = time.perf_counter() - t0
             while inflight and inflight[0][1].query():
-                r, ev, out = inflight.popleft()
+                r, ev, out, ev_s = inflight.popleft()
                 r.t_done = ev0.elapsed_time(ev) * 1e-3
+                r.t_start = ev0.elapsed_time(ev_s) * 1e-3
                 if self.keep:
                     r.result = out
             if pending and pending[0].arrival <= now:
                 r = pending.popleft()
                 idx[r.rid] = len(idx)
+                ev_s = torch.cuda.Event(enable_timing=True)
                 with torch.cuda.stream(self.stream):
                     dm, out = _alloc_and_generate(torch, r, self.device, self.stream, self.want)
+                    ev_s.record(self.stream)
                     st_ = self.b.launch(dm, self.want, out, ws=self.ws, ws_bytes=self.ws_bytes, stream=self.stream,
                                         status=status[idx[r.rid]:idx[r.rid] + 1])
                 if st_:
                     raise nn.NNError(st_, "plain build")
                 ev = torch.cuda.Event(enable_timing=True)
                 ev.record(self.stream)
-                inflight.append((r, ev, out))
+                inflight.append((r, ev, out, ev_s))
                 continue
             if inflight:
                 time.sleep(20e-6)
