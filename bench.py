@@ -43,7 +43,8 @@ WORKLOADS = {
                     "40 GB device-memory budget; batched continuous serving vs one build per mesh"),
 }
 WANT = {"both": 3, "nodes": 1, "elems": 2}
-KERNEL_OF_STAGE = {"hist": "k_hist", "offsets": "k_offsets", "part": "k_part", "bucket": "k_bucket"}
+KERNEL_OF_STAGE = {"hist": "k_hist", "offsets": "k_offsets", "part": "k_part", "bucket": "k_bucket",
+                   "place": "k_node_scan+k_node_copy"}
 
 
 def parse():
@@ -407,6 +408,7 @@ def main():
         "offsets": 3 * 4 * G * B + 4 * (B + 1),
         "part": 4 * n_conn + 4 * G * B + rb * n_conn,
         "bucket": rb * n_conn + 4 * (B + 1) + out_bytes,
+        "place": (8 * (N + 1) + 4 * nnz["nodes"]) if "nodes" in nnz else 0,
     }
     pipeline_bytes = 4 * n_conn + out_bytes      # read connectivity once, write the CSRs once
     peak, peak_src = measured_peaks()
@@ -456,7 +458,7 @@ def main():
                      "step_ms_median": per_step[len(per_step) // 2],
                      "step_ms_p95": per_step[min(len(per_step) - 1, int(0.95 * len(per_step)))],
                      "wall_s": t_wall},
-        "gpu_launches": launches_per_build(plan) * args.steps,
+        "gpu_launches": launches_per_build(plan, args.want) * args.steps,
         "clocks": clocks,
         "e2e": e2e,
         "cpu_baseline": baseline,
@@ -526,10 +528,11 @@ def whole_job_value(n_elems, steps, world, total_ms):
     return world * n_elems * steps / (total_ms * 1e-3) / 1e6
 
 
-def launches_per_build(plan):
+def launches_per_build(plan, want="both"):
     """Kernels one build launches: histogram, offsets, partition (one pass, or
-    coarse + fine when the buckets span more than 256 coarse digits), bucket."""
-    return 3 + (2 if plan["partition"] > 0 else 1)
+    coarse + fine when the buckets span more than 256 coarse digits), bucket,
+    and for node rows their placement (scan + copy)."""
+    return 3 + (2 if plan["partition"] > 0 else 1) + (2 if want in ("both", "nodes") else 0)
 
 
 def source_digest():

@@ -195,7 +195,10 @@ nn_status nn_generate_grid(int32_t type, int64_t n, uint64_t seed, int permute_n
  *   3 partition (record write), 4 bucket build (rows + CSR write).
  * nn_profile_read waits for the recorded events and returns, per stage, the
  * summed milliseconds over the calls since profiling was enabled, and the
- * number of calls.  n_stages <= 5.  Enabling twice resets the sums. */
+ * number of calls.  n_stages <= NN_PROFILE_STAGES.  Enabling twice resets the
+ * sums.  Stages: status and workspace init, histogram, offsets, partition,
+ * bucket pass, node-row placement. */
+#define NN_PROFILE_STAGES 6
 nn_status nn_profile_enable(nn_handle* h, int enable);
 nn_status nn_profile_read(nn_handle* h, double* ms, int64_t* calls, int n_stages);
 

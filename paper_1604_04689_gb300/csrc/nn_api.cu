@@ -26,8 +26,8 @@ struct nn_handle {
     // per-stage timing (nn_profile_*)
     bool prof = false;
     bool pending = false;
-    cudaEvent_t ev[6] = {};
-    double acc[5] = {};
+    cudaEvent_t ev[NN_PROFILE_STAGES + 1] = {};
+    double acc[NN_PROFILE_STAGES] = {};
     int64_t calls = 0;
 };
 
@@ -56,8 +56,7 @@ struct Plan {
     int G_part = 1;
     int G_fine = 1;
     size_t emit_smem = 0;
-    size_t off_estart = 0, off_nfc = 0, outbox_bytes = 0;
-    uint32_t outbox_words = 0;
+    size_t off_estart = 0, off_nfc = 0, off_ntmp = 0, off_ubk = 0, off_nloc = 0, off_nstart = 0, off_lb_ns = 0;
     size_t off_hist = 0, off_bstart = 0, off_gcur = 0, off_gcur_c = 0, off_rec_tmp = 0, off_rec = 0, off_lb_off = 0, off_lb_n = 0, off_lb_e = 0,
            off_ctrl = 0, off_spill = 0, zero_begin = 0, zero_end = 0;
     size_t ws_min = 0, ws_rec = 0;
@@ -185,9 +184,22 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     p.off_gcur_c = o; o = align_up(o + 256 * 4);
     p.off_rec_tmp = o; o = align_up(o + (f.cshift > 0 ? (size_t)p.n_conn * f.rb : 0));
     p.off_rec = o; o = align_up(o + (size_t)p.n_conn * f.rb);
+    // node rows in scratch (at most k per record), per-node offsets within
+    // their bucket, bucket totals and their scan
+    const bool wn = want & NN_WANT_NODES;
+    const size_t ntmp_bytes = wn ? (size_t)p.k * p.n_conn * 4 + 16 : 0;
+    if (f.cshift > 0 && (size_t)p.n_conn * f.rb >= ntmp_bytes) {
+        p.off_ntmp = p.off_rec_tmp;  // the coarse-sorted records are dead once the fine pass has run
+    } else {
+        p.off_ntmp = o; o = align_up(o + ntmp_bytes);
+    }
+    p.off_ubk = o; o = align_up(o + (wn ? (size_t)p.B * 4 : 0));
+    p.off_nloc = o; o = align_up(o + (wn ? ((size_t)p.B << sb) * 4 : 0));
+    p.off_nstart = o; o = align_up(o + (wn ? ((size_t)p.B + 1) * 8 : 0));
     p.zero_begin = o;
     p.off_nfc = o; o = align_up(o + ((want & NN_WANT_ELEMS) ? (size_t)p.B * 4 : 0));
     p.off_lb_off = o; o = align_up(o + (size_t)((p.B + OFFSETS_THREADS - 1) / OFFSETS_THREADS) * 8 + 8);
+    p.off_lb_ns = o; o = align_up(o + (wn ? (size_t)((p.B + 127) / 128) * 8 + 8 : 0));
     p.off_lb_n = o; o = align_up(o + ((want & NN_WANT_NODES) ? (size_t)p.B * 8 : 0));
     p.off_lb_e = o; o = align_up(o + ((want & NN_WANT_ELEMS) ? (size_t)p.B * 8 : 0));
     p.off_ctrl = o; o = align_up(o + 64);
@@ -195,14 +207,7 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     p.off_spill = o;
     p.ws_min = o;
     const size_t spill = ((size_t)16 << 20) + (size_t)p.n_conn * 8;
-    // bucket CTAs' outboxes (node offsets and rows of a bucket awaiting its
-    // offset; room for a little more than the average distinct-neighbour
-    // count per node, a bucket with more writes its rows without parking
-    // them), at the end of the workspace when it has room beside the spill
-    // area; without them every bucket writes its rows as soon as it can
-    p.outbox_words = (want & NN_WANT_NODES) ? std::min<uint32_t>(p.area_words, (uint32_t)(p.wide ? 20 : 10) << sb) : 0;
-    p.outbox_bytes = p.outbox_words ? align_up((size_t)p.bucket_grid * (((size_t)1 << sb) + p.outbox_words) * 4) : 0;
-    p.ws_rec = o + spill + p.outbox_bytes;
+    p.ws_rec = o + spill;
 
     *P = p;
     return NN_OK;
@@ -211,8 +216,8 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
 void prof_flush(nn_handle* h) {
     if (!h->pending) return;
     h->pending = false;
-    if (cudaEventSynchronize(h->ev[5]) != cudaSuccess) return;
-    for (int i = 0; i < 5; ++i) {
+    if (cudaEventSynchronize(h->ev[NN_PROFILE_STAGES]) != cudaSuccess) return;
+    for (int i = 0; i < NN_PROFILE_STAGES; ++i) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]) == cudaSuccess) h->acc[i] += ms;
     }
@@ -299,13 +304,7 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
     bp.ticket = ctrl + 1;
     bp.spill_cursor = reinterpret_cast<unsigned long long*>(ctrl + 2);
     bp.spill = reinterpret_cast<uint32_t*>(w + p.off_spill);
-    size_t spill_bytes = ws_bytes > p.off_spill ? ws_bytes - p.off_spill : 0;
-    if (p.outbox_bytes && spill_bytes >= p.outbox_bytes + ((size_t)16 << 20)) {
-        const size_t ob = (ws_bytes - p.outbox_bytes) & ~(ALIGN - 1);
-        bp.outbox = reinterpret_cast<uint32_t*>(w + ob);
-        bp.outbox_words = p.outbox_words;
-        spill_bytes = ob - p.off_spill;
-    }
+    const size_t spill_bytes = ws_bytes > p.off_spill ? ws_bytes - p.off_spill : 0;
     bp.spill_words = spill_bytes / 4;
     if (want & NN_WANT_NODES) {
         bp.rp_n = nodes->row_ptr;
@@ -320,6 +319,9 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
     bp.status = d_status;
     bp.area_words = p.area_words;
     bp.wide = p.wide;
+    bp.ntmp = reinterpret_cast<uint32_t*>(w + p.off_ntmp);
+    bp.ubk = reinterpret_cast<uint32_t*>(w + p.off_ubk);
+    bp.nloc = reinterpret_cast<uint32_t*>(w + p.off_nloc);
 
     prof_mark(h, 1, s);
     if (launch_hist(ep, p.emit_smem, s) != cudaSuccess) return NN_ERR_CUDA;
@@ -335,6 +337,28 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
     if (launch_bucket(bp, p.bucket_grid, p.bucket_threads, p.bucket_smem, s) != cudaSuccess)
         return NN_ERR_CUDA;
     prof_mark(h, 5, s);
+    if (want & NN_WANT_NODES) {
+        CompactParams cp{};
+        cp.n_buckets = p.B;
+        cp.n_buckets_cap = p.B;
+        cp.sb = p.fmt.sb;
+        cp.k = p.k;
+        cp.n_nodes = p.N;
+        cp.bstart = bp.bstart;
+        cp.ubk = bp.ubk;
+        cp.nloc = bp.nloc;
+        cp.ntmp = bp.ntmp;
+        cp.nstart = reinterpret_cast<uint64_t*>(w + p.off_nstart);
+        cp.lb_state = reinterpret_cast<uint64_t*>(w + p.off_lb_ns);
+        cp.ticket = ctrl + 4;
+        cp.rp_n = nodes->row_ptr;
+        cp.col_n = nodes->col;
+        cp.cap_n = nodes->col_capacity;
+        cp.status = d_status;
+        if (launch_node_compact(cp, (int)std::min<int64_t>(p.B, (int64_t)h->sms * 8), s) != cudaSuccess)
+            return NN_ERR_CUDA;
+    }
+    prof_mark(h, 6, s);
     if (h->prof) h->pending = true;
     return NN_OK;
 }
@@ -346,9 +370,10 @@ struct BatchPlan {
     int64_t B_cap = 0;
     size_t hdr_bytes = 0, meshes_off = 0, elem_off_off = 0, bucket_off_off = 0, table_bytes = 0;
     size_t off_bcount = 0, off_bstart = 0, off_gcur = 0, off_rec = 0, off_lb_off = 0, off_lb_n = 0,
-           off_lb_e = 0, off_ctrl = 0, off_spill = 0, ws_min = 0, ws_rec = 0, outbox_bytes = 0;
+           off_lb_e = 0, off_ctrl = 0, off_spill = 0, ws_min = 0, ws_rec = 0, off_nfc = 0,
+           off_estart = 0, off_ntmp = 0, off_ubk = 0, off_nloc = 0, off_nstart = 0, off_lb_ns = 0;
     size_t bucket_smem = 0;
-    uint32_t area_words = 0, outbox_words = 0;
+    uint32_t area_words = 0;
     int bucket_grid = 0, emit_grid = 0, bucket_threads = 128;
     int64_t tiles_cap = 0;
 };
@@ -380,19 +405,25 @@ nn_status batch_plan(const nn_handle* h, const nn_batch_caps* c, BatchPlan* out)
     p.bucket_grid = h->sms * per_sm;
     size_t o = p.table_bytes;
     p.off_bcount = o; o = align_up(o + (size_t)p.B_cap * 4);
+    p.off_nfc = o; o = align_up(o + (size_t)p.B_cap * 4);
     p.off_bstart = o; o = align_up(o + ((size_t)p.B_cap + 1) * 4);
+    p.off_estart = o; o = align_up(o + ((size_t)p.B_cap + 1) * 4);
     p.off_gcur = o; o = align_up(o + (size_t)p.B_cap * 4);
     p.off_rec = o; o = align_up(o + (size_t)c->max_conn * 16);
+    const bool wn = c->want & NN_WANT_NODES;
+    p.off_ntmp = o; o = align_up(o + (wn ? (size_t)3 * c->max_conn * 4 + 16 : 0));
+    p.off_ubk = o; o = align_up(o + (wn ? (size_t)p.B_cap * 4 : 0));
+    p.off_nloc = o; o = align_up(o + (wn ? ((size_t)p.B_cap << p.sb) * 4 : 0));
+    p.off_nstart = o; o = align_up(o + (wn ? ((size_t)p.B_cap + 1) * 8 : 0));
+    p.off_lb_ns = o; o = align_up(o + (wn ? (size_t)((p.B_cap + 127) / 128) * 8 + 8 : 0));
     p.tiles_cap = (p.B_cap + OFFSETS_THREADS - 1) / OFFSETS_THREADS;
     p.off_lb_off = o; o = align_up(o + ((size_t)p.tiles_cap + 1) * 8);
     p.off_lb_n = o; o = align_up(o + (size_t)p.B_cap * 8);
     p.off_lb_e = o; o = align_up(o + (size_t)p.B_cap * 8);
     p.off_ctrl = o; o = align_up(o + 64);
-    p.outbox_words = std::min<uint32_t>(p.area_words, 20u << p.sb);
     p.off_spill = o;
     p.ws_min = o;
-    p.outbox_bytes = align_up((size_t)p.bucket_grid * (((size_t)1 << p.sb) + p.outbox_words) * 4);
-    p.ws_rec = o + (((size_t)16 << 20) + (size_t)c->max_conn * 8) + p.outbox_bytes;
+    p.ws_rec = o + (((size_t)16 << 20) + (size_t)c->max_conn * 8);
     p.emit_grid = h->sms * (2048 / batch_threads());
     *out = p;
     return NN_OK;
@@ -486,21 +517,25 @@ nn_status batch_launch(nn_handle* h, const nn_batch_caps* c, const void* staging
     bt.elem_off = reinterpret_cast<const int64_t*>(w + bp.elem_off_off);
     bt.bucket_off = reinterpret_cast<const int64_t*>(w + bp.bucket_off_off);
     uint32_t* bcount = reinterpret_cast<uint32_t*>(w + bp.off_bcount);
+    uint32_t* nfc = reinterpret_cast<uint32_t*>(w + bp.off_nfc);
     uint32_t* gcur = reinterpret_cast<uint32_t*>(w + bp.off_gcur);
     uint32_t* ctrl = reinterpret_cast<uint32_t*>(w + bp.off_ctrl);
     uint64_t* lb_off = reinterpret_cast<uint64_t*>(w + bp.off_lb_off);
     uint64_t* lb_n = reinterpret_cast<uint64_t*>(w + bp.off_lb_n);
     uint64_t* lb_e = reinterpret_cast<uint64_t*>(w + bp.off_lb_e);
     uint8_t* rec = w + bp.off_rec;
-    if (launch_batch_emit(bt, bcount, gcur, rec, lb_off, lb_n, lb_e, ctrl, bp.emit_grid, 0, s) != cudaSuccess)
+    if (launch_batch_emit(bt, bcount, nfc, gcur, rec, lb_off, lb_n, lb_e, ctrl, bp.emit_grid, 0, s,
+                          reinterpret_cast<uint64_t*>(w + bp.off_lb_ns)) != cudaSuccess)
         return NN_ERR_CUDA;
-    if (launch_batch_emit(bt, bcount, gcur, rec, lb_off, lb_n, lb_e, ctrl, bp.emit_grid, 1, s) != cudaSuccess)
+    if (launch_batch_emit(bt, bcount, nfc, gcur, rec, lb_off, lb_n, lb_e, ctrl, bp.emit_grid, 1, s) != cudaSuccess)
         return NN_ERR_CUDA;
     OffsetsParams op{};
     op.hist = bcount;
     op.n_cta = 1;
     op.n_buckets = bp.B_cap;
     op.bstart = reinterpret_cast<uint32_t*>(w + bp.off_bstart);
+    op.nfc = nfc;
+    op.estart = (c->want & NN_WANT_ELEMS) ? reinterpret_cast<uint32_t*>(w + bp.off_estart) : nullptr;
     op.gcur = gcur;
     op.lb_state = lb_off;
     op.ticket = ctrl + 0;
@@ -508,24 +543,19 @@ nn_status batch_launch(nn_handle* h, const nn_batch_caps* c, const void* staging
     op.status = reinterpret_cast<int32_t*>(ctrl + 8);  // passed on to every mesh by the bucket pass
     op.hdr = bt.hdr;
     if (launch_offsets(op, s) != cudaSuccess) return NN_ERR_CUDA;
-    if (launch_batch_emit(bt, bcount, gcur, rec, lb_off, lb_n, lb_e, ctrl, bp.emit_grid, 2, s) != cudaSuccess)
+    if (launch_batch_emit(bt, bcount, nfc, gcur, rec, lb_off, lb_n, lb_e, ctrl, bp.emit_grid, 2, s) != cudaSuccess)
         return NN_ERR_CUDA;
     BucketParams kp{};
     kp.n_buckets = 0;
     kp.rec = rec;
     kp.bstart = op.bstart;
+    kp.estart = op.estart;
     kp.lb_n = lb_n;
     kp.lb_e = lb_e;
     kp.ticket = ctrl + 1;
     kp.spill_cursor = reinterpret_cast<unsigned long long*>(ctrl + 2);
     kp.spill = reinterpret_cast<uint32_t*>(w + bp.off_spill);
-    size_t spill_bytes = ws_bytes > bp.off_spill ? ws_bytes - bp.off_spill : 0;
-    if (spill_bytes >= bp.outbox_bytes + ((size_t)16 << 20)) {
-        const size_t ob = (ws_bytes - bp.outbox_bytes) & ~(ALIGN - 1);
-        kp.outbox = reinterpret_cast<uint32_t*>(w + ob);
-        kp.outbox_words = bp.outbox_words;
-        spill_bytes = ob - bp.off_spill;
-    }
+    const size_t spill_bytes = ws_bytes > bp.off_spill ? ws_bytes - bp.off_spill : 0;
     kp.spill_words = spill_bytes / 4;
     kp.area_words = bp.area_words;
     kp.batch = bt;
@@ -533,7 +563,24 @@ nn_status batch_launch(nn_handle* h, const nn_batch_caps* c, const void* staging
     kp.fmt.rb = 16;
     kp.fmt.k = 3;
     kp.wide = 1;
+    kp.ntmp = reinterpret_cast<uint32_t*>(w + bp.off_ntmp);
+    kp.ubk = reinterpret_cast<uint32_t*>(w + bp.off_ubk);
+    kp.nloc = reinterpret_cast<uint32_t*>(w + bp.off_nloc);
     if (launch_bucket(kp, bp.bucket_grid, bp.bucket_threads, bp.bucket_smem, s) != cudaSuccess) return NN_ERR_CUDA;
+    if (c->want & NN_WANT_NODES) {
+        CompactParams cp{};
+        cp.n_buckets_cap = bp.B_cap;
+        cp.bstart = kp.bstart;
+        cp.ubk = kp.ubk;
+        cp.nloc = kp.nloc;
+        cp.ntmp = kp.ntmp;
+        cp.nstart = reinterpret_cast<uint64_t*>(w + bp.off_nstart);
+        cp.lb_state = reinterpret_cast<uint64_t*>(w + bp.off_lb_ns);
+        cp.ticket = ctrl + 4;
+        cp.status = reinterpret_cast<int32_t*>(ctrl + 8);
+        cp.batch = bt;
+        if (launch_node_compact(cp, h->sms * 8, s) != cudaSuccess) return NN_ERR_CUDA;
+    }
     return NN_OK;
 }
 
@@ -613,7 +660,7 @@ nn_status nn_profile_enable(nn_handle* h, int enable) {
 }
 
 nn_status nn_profile_read(nn_handle* h, double* ms, int64_t* calls, int n_stages) {
-    if (!h || n_stages < 0 || n_stages > 5) return NN_ERR_ARG;
+    if (!h || n_stages < 0 || n_stages > NN_PROFILE_STAGES) return NN_ERR_ARG;
     prof_flush(h);
     for (int i = 0; i < n_stages; ++i) ms[i] = h->acc[i];
     if (calls) *calls = h->calls;

@@ -91,19 +91,22 @@ __device__ __forceinline__ void walk_batch(const BatchTables& bt, F&& f) {
     }
 }
 
-__global__ void __launch_bounds__(BATCH_THREADS) k_batch_init(BatchTables bt, uint32_t* bcount,
+__global__ void __launch_bounds__(BATCH_THREADS) k_batch_init(BatchTables bt, uint32_t* bcount, uint32_t* nfc,
                                                               uint64_t* lb_off, uint64_t* lb_n,
-                                                              uint64_t* lb_e, uint32_t* ctrl) {
+                                                              uint64_t* lb_e, uint32_t* ctrl, uint64_t* lb_ns) {
     const int64_t B = bt.hdr->n_buckets;
     const int64_t tiles = (B + OFFSETS_THREADS - 1) / OFFSETS_THREADS;
     const int n = bt.hdr->n_meshes;
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = i0; i < B; i += st) {
         bcount[i] = 0;
+        nfc[i] = 0;
         lb_n[i] = 0;
         lb_e[i] = 0;
     }
     for (int64_t i = i0; i < tiles + 1; i += st) lb_off[i] = 0;
+    if (lb_ns)
+        for (int64_t i = i0; i < (B + 127) / 128 + 1; i += st) lb_ns[i] = 0;
     for (int64_t i = i0; i < 16; i += st) ctrl[i] = 0;
     for (int64_t i = i0; i < n; i += st) {
         const BatchMesh& M = bt.meshes[i];
@@ -115,14 +118,23 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch_init(BatchTables bt, ui
     }
 }
 
-__global__ void __launch_bounds__(BATCH_THREADS) k_hist_b(BatchTables bt, uint32_t* bcount) {
+// Records per bucket, and (rare) records of a node already seen in its
+// element, which add no element entry.
+__global__ void __launch_bounds__(BATCH_THREADS) k_hist_b(BatchTables bt, uint32_t* bcount, uint32_t* nfc) {
     const int sb = bt.hdr->fmt.sb;
     walk_batch(bt, [&](int m, const BatchMesh& M, int64_t, int t, const int32_t* nd) {
         const int npe = npe_of(t);
         uint32_t* cnt = bcount + bt.bucket_off[m];
+        uint32_t* rep = nfc + bt.bucket_off[m];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            if (i < npe) atomicAdd(&cnt[(uint32_t)nd[i] >> sb], 1u);
+        for (int i = 0; i < 8; ++i) {
+            if (i >= npe) break;
+            atomicAdd(&cnt[(uint32_t)nd[i] >> sb], 1u);
+            int nf = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) nf |= (q < i) && (nd[q] == nd[i]);
+            if (nf) atomicAdd(&rep[(uint32_t)nd[i] >> sb], 1u);
+        }
     });
 }
 
@@ -163,11 +175,11 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_part_b(BatchTables bt, uint32
 
 }  // namespace
 
-cudaError_t launch_batch_emit(const BatchTables& bt, uint32_t* bcount, uint32_t* gcur, uint8_t* rec,
+cudaError_t launch_batch_emit(const BatchTables& bt, uint32_t* bcount, uint32_t* nfc, uint32_t* gcur, uint8_t* rec,
                               uint64_t* lb_off, uint64_t* lb_n, uint64_t* lb_e, uint32_t* ctrl, int grid,
-                              int stage, cudaStream_t s) {
-    if (stage == 0) k_batch_init<<<grid, BATCH_THREADS, 0, s>>>(bt, bcount, lb_off, lb_n, lb_e, ctrl);
-    else if (stage == 1) k_hist_b<<<grid, BATCH_THREADS, 0, s>>>(bt, bcount);
+                              int stage, cudaStream_t s, uint64_t* lb_ns) {
+    if (stage == 0) k_batch_init<<<grid, BATCH_THREADS, 0, s>>>(bt, bcount, nfc, lb_off, lb_n, lb_e, ctrl, lb_ns);
+    else if (stage == 1) k_hist_b<<<grid, BATCH_THREADS, 0, s>>>(bt, bcount, nfc);
     else k_part_b<<<grid, BATCH_THREADS, 0, s>>>(bt, gcur, rec);
     return cudaGetLastError();
 }

@@ -15,8 +15,11 @@
 //      segment of shared memory.  A node with more records or distinct
 //      neighbours than the registers hold is finished by its whole warp in
 //      global scratch memory (bitonic sort, then adjacent-duplicate removal).
-//   4. writes row_ptr and col of both CSRs at offsets found by a lookback scan
-//      over the buckets, which are taken in node order.
+//   4. writes the element CSR at offsets known before the pass (a prefix of
+//      the record counts), and leaves the node rows, each node's offset within
+//      them and their total in a scratch area, at a position bounded in
+//      advance (K times the bucket's first record); the compaction pass
+//      places them (nn_compact.cu).  No bucket ever waits for another.
 // A bucket whose record groups and element rows do not fit shared memory
 // keeps them in a global spill area; so does a group whose distinct-neighbour
 // rows do not fit.
@@ -163,16 +166,6 @@ struct BucketOut {
     int32_t* status;
 };
 
-// A bucket whose node rows wait in the CTA's outbox for their offset.
-struct Pending {
-    int64_t b, first, v0, N;
-    uint64_t Ub, Gn;
-    int nb;
-    bool valid, last;
-    int64_t* rp_n; int32_t* col_n; int64_t cap_n;
-    int32_t* status;
-};
-
 // Shared memory: per node cnt (u64) and gcur (u32); per group gseg, gtot,
 // gpre (64 each); scan scratch (34 u64); misc (8 u64); the warps' tables;
 // then the area (record groups, element rows, distinct-neighbour segments).
@@ -187,7 +180,6 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_bucket(BucketParams 
     constexpr int CH = chunk<IMAX>();
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ BucketOut sh_out;
-    __shared__ Pending pend;
     const bool batched = p.batch.hdr != nullptr;
     const RecFmt f = batched ? p.batch.hdr->fmt : p.fmt;
     const int64_t n_buckets = batched ? p.batch.hdr->n_buckets : p.n_buckets;
@@ -207,33 +199,7 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_bucket(BucketParams 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t* const tabw = tabs + warp * (HT * 32) + lane;
 
-    uint32_t* const ob_off = p.outbox ? p.outbox + (size_t)blockIdx.x * ((size_t)NB + p.outbox_words) : nullptr;
-    uint32_t* const ob_rows = ob_off ? ob_off + NB : nullptr;
-    // node rows of the pending bucket: offset resolved (warp 0) ...
-    auto pend_resolve = [&]() {
-        if (warp == 0 && pend.valid) {
-            const uint64_t gn = lb_resolve_wide<8>(p.lb_n, pend.b, pend.Ub, pend.status, pend.first);
-            if (lane == 0) {
-                pend.Gn = gn;
-                if (gn + pend.Ub > (uint64_t)pend.cap_n) set_status(pend.status, NN_ERR_CAPACITY);
-            }
-        }
-    };
-    // ... then written out of the outbox (all threads, after a barrier)
-    auto pend_flush = [&]() {
-        if (!pend.valid) return;
-        const uint64_t gn = pend.Gn, ub = pend.Ub;
-        for (int l = tid; l < pend.nb; l += THREADS) pend.rp_n[pend.v0 + l] = (int64_t)(gn + ob_off[l]);
-        if (gn + ub <= (uint64_t)pend.cap_n) {
-            int32_t* dst = pend.col_n + gn;
-            for (uint32_t i = tid; i < ub; i += THREADS) dst[i] = (int32_t)ob_rows[i];
-        }
-        if (pend.last && tid == 0) pend.rp_n[pend.N] = (int64_t)(gn + ub);
-    };
-    if (tid == 0) {
-        misc[0] = atomicAdd(p.ticket, 1u);
-        pend.valid = false;
-    }
+    if (tid == 0) misc[0] = atomicAdd(p.ticket, 1u);
     __syncthreads();
     int64_t b_next = (int64_t)misc[0];
     __syncthreads();
@@ -332,17 +298,17 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_bucket(BucketParams 
         const uint64_t ucap = insm ? (uint64_t)p.area_words - R - Eb : (uint64_t)p.area_words;
 
         // the element rows' offset: a prefix of the record counts, known
-        // before this pass; for batches, a lookback over the buckets that warp
-        // 0 resolves now (its predecessors published long ago) while the
-        // others group records
+        // before this pass (for a batch, relative to the mesh's first bucket);
+        // without it, a lookback over the buckets that warp 0 resolves while
+        // the others group records
         if (warp == 0 && want_e) {
-            const uint64_t ge = p.estart ? (uint64_t)p.estart[b] : lb_resolve_wide<4>(p.lb_e, b, Eb, status, first);
+            const uint64_t ge = p.estart ? (uint64_t)(p.estart[b] - p.estart[first])
+                                         : lb_resolve_wide<4>(p.lb_e, b, Eb, status, first);
             if (lane == 0) {
                 misc[1] = ge;
                 if (ge + Eb > (uint64_t)sh_out.cap_e) set_status(status, NN_ERR_CAPACITY);
             }
         }
-        pend_resolve();
         // 2. record indices grouped by node (a node with more than 2^21
         // records in one bucket cannot be stashed: any slot that large is
         // simply counted again)
@@ -369,7 +335,6 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_bucket(BucketParams 
         }
         __syncthreads();
 
-        pend_flush();
         // 3. one lane per node, one warp per group of 32 nodes
         const int ng = (nb + 31) >> 5;
         for (int g = warp; ok && g < ng; g += W) {
@@ -572,9 +537,9 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_bucket(BucketParams 
         }
         __syncthreads();
 
-        // 4. element rows out; node rows published and parked in the outbox
-        // (their offset is resolved while the next bucket is grouped, when
-        // the predecessors have long published), or written now if too many
+        // 4. element rows to their offset; node rows, with each node's offset
+        // within the bucket and the bucket's total, to the scratch area (their
+        // offsets are placed by the compaction pass, so no bucket waits here)
         const uint64_t Ge = misc[1];
         if (warp == 0) {
             const int NG = (NB + 31) >> 5;  // <= 64
@@ -590,27 +555,9 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_bucket(BucketParams 
             }
             const uint32_t t0 = __shfl_sync(FULL, s0, 31);
             s1 += t0;
-            const uint64_t Ub = __shfl_sync(FULL, s1, 31);
             if (lane < NG) gpre[lane] = s0 - a0;
             if (lane + 32 < NG) gpre[lane + 32] = s1 - a1;
-            if (want_n && lane == 0) lb_publish(p.lb_n, b, Ub, first);
-            if (lane == 0) {
-                misc[7] = Ub;
-                pend.valid = want_n;
-                if (want_n) {  // the rows of this bucket wait for their offset
-                    pend.b = b;
-                    pend.first = first;
-                    pend.v0 = v0;
-                    pend.N = N;
-                    pend.Ub = Ub;
-                    pend.nb = nb;
-                    pend.last = sh_out.last;
-                    pend.rp_n = sh_out.rp_n;
-                    pend.col_n = sh_out.col_n;
-                    pend.cap_n = sh_out.cap_n;
-                    pend.status = status;
-                }
-            }
+            if (want_n && lane == 31) p.ubk[b] = s1;
         } else if (want_e) {
             const bool e_ok = ok && Ge + Eb <= (uint64_t)sh_out.cap_e;
             for (int l = tid - 32; l < nb; l += THREADS - 32)
@@ -621,48 +568,22 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_bucket(BucketParams 
             }
         }
         __syncthreads();
-        const uint64_t Ub = misc[7];
         if (want_n) {
-            const bool park = p.outbox != nullptr && Ub <= p.outbox_words;
-            uint32_t* const rows = park ? ob_rows : nullptr;
-            if (!park) {  // too many to park: resolve now and write in place
-                pend_resolve();
-                __syncthreads();
-            }
-            const uint64_t Gn = park ? 0 : pend.Gn;
-            const bool n_ok = ok && (park || Gn + Ub <= (uint64_t)sh_out.cap_n);
-            for (int l = tid; l < nb; l += THREADS) {
-                const uint32_t o = gpre[l >> 5] + gcur[l];
-                if (park) ob_off[l] = o;
-                else sh_out.rp_n[v0 + l] = (int64_t)(Gn + o);
-            }
-            if (n_ok) {
-                for (int g = warp; g < ng; g += W) {
-                    const uint32_t seg = gseg[g], n = gtot[g];
-                    if (seg == SEG_NONE) continue;
-                    const uint32_t* src = (seg & SEG_SPILL) ? p.spill + (seg & ~SEG_SPILL) : Ust + seg;
-                    if (park) {
-                        uint32_t* dst = rows + gpre[g];
-                        for (uint32_t i = lane; i < n; i += 32) dst[i] = src[i];
-                    } else {
-                        int32_t* dst = sh_out.col_n + Gn + gpre[g];
-                        for (uint32_t i = lane; i < n; i += 32) dst[i] = (int32_t)src[i];
-                    }
-                }
-            }
-            if (!park) {
-                if (sh_out.last && tid == 0) sh_out.rp_n[N] = (int64_t)(Gn + Ub);
-                __syncthreads();
-                if (tid == 0) pend.valid = false;
+            uint32_t* const loc = p.nloc + ((size_t)b << f.sb);
+            for (int l = tid; l < nb; l += THREADS) loc[l] = gpre[l >> 5] + gcur[l];
+            uint32_t* const rows = p.ntmp + (size_t)K * r0;
+            for (int g = warp; ok && g < ng; g += W) {
+                const uint32_t seg = gseg[g], n = gtot[g];
+                if (seg == SEG_NONE) continue;
+                const uint32_t* src = (seg & SEG_SPILL) ? p.spill + (seg & ~SEG_SPILL) : Ust + seg;
+                uint32_t* dst = rows + gpre[g];
+                for (uint32_t i = lane; i < n; i += 32) dst[i] = src[i];
             }
         }
         if (sh_out.last && tid == 0 && want_e) sh_out.rp_e[N] = (int64_t)(Ge + Eb);
         b_next = (int64_t)misc[5];
         __syncthreads();
     }
-    pend_resolve();
-    __syncthreads();
-    pend_flush();
 }
 
 // Allow up to `bytes` of dynamic shared memory, less the kernel's own static

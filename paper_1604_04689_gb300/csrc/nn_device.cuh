@@ -134,10 +134,13 @@ __device__ inline uint64_t lb_resolve(uint64_t* state, uint64_t t, uint64_t agg,
 // As lb_resolve, but every lane reads V consecutive predecessors per step
 // (32 V per step): when hundreds of tiles are in flight, the nearest
 // inclusive prefix is that far back, and each step is an L2 round trip.
+// Non-blocking (blocking = false): gives up, publishing nothing, at the first
+// predecessor that is not ready, and reports *ok = false.
 template <int V>
 __device__ inline uint64_t lb_resolve_wide(uint64_t* state, uint64_t t, uint64_t agg, int32_t* status,
-                                           uint64_t first = 0) {
+                                           uint64_t first = 0, bool blocking = true, bool* ok = nullptr) {
     const int lane = threadIdx.x & 31;
+    if (ok) *ok = true;
     if (t == first) return 0;
     uint64_t excl = 0;
     int64_t p = (int64_t)t - 1;  // nearest predecessor not yet consumed
@@ -172,6 +175,10 @@ __device__ inline uint64_t lb_resolve_wide(uint64_t* state, uint64_t t, uint64_t
         if (done) break;
         p -= k_nr;
         if (k_nr == 0) {  // nearest predecessor not ready yet: bounded wait
+            if (!blocking) {
+                if (ok) *ok = false;
+                return 0;
+            }
             const uint64_t now = global_ns();
             if (t0 == 0) {
                 t0 = now;

@@ -117,7 +117,7 @@ struct BucketParams {
     int64_t n_buckets;
     const uint8_t* rec;
     const uint32_t* bstart;
-    const uint32_t* estart; // element-CSR offset of each bucket (nullptr: found by lookback in lb_e)
+    const uint32_t* estart; // element-CSR offset of each bucket, batch-wide (nullptr: found by lookback in lb_e)
     uint64_t* lb_n;         // lookback words, node CSR, one per bucket
     uint64_t* lb_e;         // lookback words, element CSR, one per bucket
     uint32_t* ticket;
@@ -128,8 +128,9 @@ struct BucketParams {
     int64_t* rp_e; int32_t* col_e; int64_t cap_e;
     int32_t* status;
     uint32_t area_words;    // shared-memory words available for record groups and rows
-    uint32_t* outbox;       // per CTA: node offsets [2^sb] then rows [outbox_words] of the bucket awaiting its offset
-    uint32_t outbox_words;
+    uint32_t* ntmp;         // node rows of bucket b at ntmp + k * bstart[b] (k = neighbours per record)
+    uint32_t* ubk;          // [n_buckets] node-row total of each bucket
+    uint32_t* nloc;         // [n_buckets << sb] each node's offset within its bucket's rows
     int32_t wide;           // 1: 32 records and a 32-slot table per node in registers, 0: 16 and 16
     BatchTables batch;      // batch.hdr != nullptr: format, bucket count and meshes come from the tables
     const int32_t* batch_err;  // batches: status of the shared offsets scan, copied to every mesh
@@ -140,7 +141,26 @@ constexpr int PART_THREADS = 512;
 constexpr int SORT_THREADS = 256;   // tile-sorted partition passes
 constexpr int OFFSETS_THREADS = 128;
 
+// Placement of the node rows the bucket pass left in scratch (nn_compact.cu).
+struct CompactParams {
+    int64_t n_buckets;       // single mesh (batches: from the header)
+    int64_t n_buckets_cap;   // grid of the scan (batches: capacity)
+    int sb, k;               // single mesh (batches: from the header; k = 3)
+    int64_t n_nodes;
+    const uint32_t* bstart;
+    const uint32_t* ubk;
+    const uint32_t* nloc;
+    const uint32_t* ntmp;
+    uint64_t* nstart;        // [n_buckets+1] exclusive scan of ubk (batch-wide)
+    uint64_t* lb_state;      // lookback words, one per tile of buckets
+    uint32_t* ticket;
+    int64_t* rp_n; int32_t* col_n; int64_t cap_n;
+    int32_t* status;
+    BatchTables batch;
+};
+
 // launchers (return the CUDA error of the launch)
+cudaError_t launch_node_compact(const CompactParams& p, int copy_grid, cudaStream_t s);
 cudaError_t launch_hist(const EmitParams& p, size_t smem, cudaStream_t s);
 cudaError_t launch_part(const EmitParams& p, cudaStream_t s);
 cudaError_t launch_part_sorted(const EmitParams& p, const uint32_t* bstart, int grid_fine, cudaStream_t s);
@@ -148,9 +168,9 @@ cudaError_t launch_offsets(const OffsetsParams& p, cudaStream_t s);
 cudaError_t launch_bucket(const BucketParams& p, int grid, int threads, size_t smem, cudaStream_t s);
 size_t bucket_fixed_bytes(int sb, int threads, int wide);  // shared memory of the bucket kernel outside its area
 cudaError_t bucket_occupancy(int* blocks, int threads, int wide, size_t smem);
-cudaError_t launch_batch_emit(const BatchTables& bt, uint32_t* bcount, uint32_t* gcur, uint8_t* rec,
+cudaError_t launch_batch_emit(const BatchTables& bt, uint32_t* bcount, uint32_t* nfc, uint32_t* gcur, uint8_t* rec,
                               uint64_t* lb_off, uint64_t* lb_n, uint64_t* lb_e, uint32_t* ctrl, int grid,
-                              int stage, cudaStream_t s);
+                              int stage, cudaStream_t s, uint64_t* lb_ns = nullptr);
 int batch_threads();
 cudaError_t set_emit_smem_all(size_t bytes);
 cudaError_t set_bucket_smem_all(size_t bytes);

@@ -228,7 +228,7 @@ def generate_grid(etype: int, n: int, seed: int, permute_nodes: bool = True, per
     return DeviceMesh(etype, N, conn)
 
 
-STAGES = ("init", "hist", "offsets", "part", "bucket")
+STAGES = ("init", "hist", "offsets", "part", "bucket", "place")
 
 
 def nn_profile_enable(h: int, enable: bool) -> None:
@@ -239,9 +239,9 @@ def nn_profile_enable(h: int, enable: bool) -> None:
 
 def nn_profile_read(h: int):
     """({stage: summed ms}, calls) since profiling was enabled."""
-    ms = (C.c_double * 5)()
+    ms = (C.c_double * len(STAGES))()
     calls = C.c_int64()
-    st = lib().nn_profile_read(h, ms, C.byref(calls), 5)
+    st = lib().nn_profile_read(h, ms, C.byref(calls), len(STAGES))
     if st:
         raise NNError(st, "nn_profile_read")
     return dict(zip(STAGES, list(ms))), calls.value

@@ -238,8 +238,8 @@ def test_workspace_errors():
     out = b2.alloc_outputs(dm, nn.WANT_BOTH)
     need, _, _ = b2.query(dm, nn.WANT_BOTH)
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
-    spill = 16 << 20
-    st = b2.launch(dm, nn.WANT_BOTH, out, ws=ws, ws_bytes=need - spill - f.n_conn * 8)
+    ws_min = nn.nn_plan_info(b2.h, dm.struct(), nn.WANT_BOTH)["ws_min"]          # no spill area at all
+    st = b2.launch(dm, nn.WANT_BOTH, out, ws=ws, ws_bytes=ws_min)
     assert st == 0
     torch.cuda.synchronize()
     assert int(b2.status.item()) == 2
