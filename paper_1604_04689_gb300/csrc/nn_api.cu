@@ -96,17 +96,18 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     // bucket kernel shape.  Every node goes to one lane, which holds up to
     // 16 (or, "wide", 32) records and a 16 (32) slot neighbour table in
     // registers; meshes whose nodes have more than ten incidences on average
-    // (tets, mixed) take the wide form with 128-thread CTAs, four per SM,
-    // the others 256-thread CTAs, two per SM.  The bucket width is then as
+    // (tets, mixed) take the wide form.  256-thread CTAs, two per SM.  The bucket width is then as
     // many nodes as fit the CTA's shared memory with room to spare for nodes
     // of higher than average valence.
     const double inc = p.N > 0 ? (double)p.n_conn / (double)p.N : 0.0;
     p.wide = inc > 10.0 ? 1 : 0;
     const int ucap = p.wide ? 24 : 12;  // distinct neighbours a lane's table takes
-    p.bucket_threads = h->tuning.bucket_threads ? h->tuning.bucket_threads : (p.wide ? 128 : 256);
+    p.bucket_threads = h->tuning.bucket_threads ? h->tuning.bucket_threads : 256;
     const int bcps = h->tuning.bucket_ctas_per_sm ? h->tuning.bucket_ctas_per_sm : (p.bucket_threads == 128 ? 4 : 2);
     size_t bsmem = std::min(h->bucket_smem, h->smem_per_sm / (size_t)bcps - 2048);
-    const double U = (want & NN_WANT_NODES) ? std::min(p.k * inc / 2.0, (double)ucap) : 0.0;
+    // distinct neighbours per node: half the candidates, at most two thirds
+    // of what a lane's table takes (a Kuhn tet grid has 14 for 72 candidates)
+    const double U = (want & NN_WANT_NODES) ? std::min(p.k * inc / 2.0, ucap * 2.0 / 3.0) : 0.0;
     const double per_node = 4.0 * (inc + ((want & NN_WANT_ELEMS) ? inc : 0.0) + U);  // groups, elements, neighbours
     // (many buckets are fine: the histogram pass counts them in chunks that
     // fit its shared memory; the hard cap below only bounds workspace tables)
@@ -116,7 +117,7 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     for (int s = SB_MAX; s >= SB_MIN; --s) {
         if (((p.N + (1ll << s) - 1) >> s) > B_lim) break;
         const double area = (double)bsmem - (double)fixed_of(s);
-        if (area > 0 && (double)(1 << s) * per_node <= 0.8 * area) {
+        if (area > 0 && (double)(1 << s) * per_node <= 0.9 * area) {
             sb = s;
             break;
         }

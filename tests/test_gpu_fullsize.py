@@ -5,6 +5,8 @@ holds at any size: rows of a seeded sample of nodes against the oracle's
 sample-only walk (bit for bit), the closed-form sizes of the structured grids,
 the sum of element rows (one entry per incidence), per-node element counts,
 sorted rows without self entries, and symmetry of the node relation."""
+import os
+
 import numpy as np
 import pytest
 
@@ -31,9 +33,16 @@ def built():
     build.build()
 
 
-def build_on_gpu(mesh, builder):
+def build_on_gpu(mesh, builder, tune=True):
+    """Build in the launch configuration the benchmark times: the autotuner's
+    choice for this mesh class (timed afresh into a scratch cache)."""
+    import tempfile
     import torch
+    from paper_1604_04689_gb300 import autotune
     dm = nn.DeviceMesh.from_host(mesh)
+    if tune:
+        with tempfile.TemporaryDirectory() as d:
+            autotune.tuned(builder, dm, nn.WANT_BOTH, path=os.path.join(d, "tune.json"))
     out = builder.alloc_outputs(dm, nn.WANT_BOTH)
     assert builder.launch(dm, nn.WANT_BOTH, out) == 0
     torch.cuda.synchronize()
