@@ -57,6 +57,10 @@ def load_library(path: str):
     lib.oracle_nnz.argtypes = [P, C.c_int]
     lib.oracle_copy.restype = None
     lib.oracle_copy.argtypes = [P, C.c_int, C.POINTER(I64), C.POINTER(I32)]
+    lib.oracle_elem_adjacency.restype = P
+    lib.oracle_elem_adjacency.argtypes = [C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.POINTER(C.c_int32),
+                                          C.POINTER(C.c_int64), C.POINTER(C.c_uint8), C.POINTER(C.c_int32),
+                                          C.c_int64]
     lib.oracle_free.restype = None
     lib.oracle_free.argtypes = [P]
     return lib
@@ -118,3 +122,19 @@ def rows(mesh, sample, want: int = BOTH, lib=None) -> dict:
     s = np.ascontiguousarray(sample, dtype=np.int32)
     h = lib.oracle_rows(*args, want, _ptr(s, C.c_int32), int(s.shape[0]))
     return _run(lib, h, want, int(s.shape[0]))
+
+
+def element_adjacency(mesh, sample=None, lib=None) -> dict:
+    """{'status': int, 'adj': (row_ptr, col)}: face neighbours of every element
+    (or of the elements in ``sample``, CSR over the sample)."""
+    lib = lib or _load()
+    args, keep = _mesh_args(mesh)
+    if sample is None:
+        h = lib.oracle_elem_adjacency(*args, None, 0)
+        n = int(mesh.n_elems)
+    else:
+        s = np.ascontiguousarray(sample, dtype=np.int32)
+        h = lib.oracle_elem_adjacency(*args, _ptr(s, C.c_int32), int(s.shape[0]))
+        n = int(s.shape[0])
+    res = _run(lib, h, ELEMS, n)
+    return {"status": res["status"], "adj": res["elems"]}

@@ -189,4 +189,63 @@ void* oracle_rows(int32_t type, int64_t n_nodes, int64_t n_elems, int64_t n_conn
     return r;
 }
 
+// Element face adjacency (the element-to-element neighbours that Sec. 1 lists
+// among the local connectivity a mesh code needs "for each node or element";
+// the paper works out only the per-node neighbours).  Faces: tri and quad
+// edges, tet triangles, hex (VTK) quads.  Elements e != f are face neighbours
+// when every node of some face of one lies in the other (a face with a
+// repeated node is no face).  For a conforming mesh this is the dual graph; a
+// hex face split into two tet triangles borders both tets.  Plain definition:
+// node -> element sets, then for every element each candidate sharing a node
+// is tested face by face.  sample == NULL: all elements, else only the
+// sampled ones (CSR over the sample, in sample order).
+void* oracle_elem_adjacency(int32_t type, int64_t n_nodes, int64_t n_elems, int64_t n_conn,
+                            const int32_t* conn, const int64_t* elem_ptr, const uint8_t* elem_type,
+                            const int32_t* sample, int64_t n_sample) {
+    static const int NF[4] = {3, 4, 4, 6};
+    static const int FS[4] = {2, 2, 3, 4};
+    static const int FACES[4][6][4] = {
+        {{0, 1}, {1, 2}, {2, 0}},
+        {{0, 1}, {1, 2}, {2, 3}, {3, 0}},
+        {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}},
+        {{0, 1, 2, 3}, {4, 5, 6, 7}, {0, 1, 5, 4}, {1, 2, 6, 5}, {2, 3, 7, 6}, {3, 0, 4, 7}},
+    };
+    MeshIn m{type, n_nodes, n_elems, n_conn, conn, elem_ptr, elem_type};
+    Result* r = new Result();
+    // every valid element's type and nodes
+    std::vector<int> et(n_elems, -1);
+    std::vector<std::vector<int32_t>> en(n_elems);
+    std::vector<std::set<int32_t>> ne(n_nodes);
+    r->status = for_each_element(m, [&](int64_t e, int t, const int32_t* nodes) {
+        et[e] = t;
+        en[e].assign(nodes, nodes + TABLES[t].npe);
+        for (int i = 0; i < TABLES[t].npe; ++i) ne[nodes[i]].insert((int32_t)e);
+    });
+    // some face of a lies in b
+    auto face_in = [&](int64_t a, int64_t b) {
+        const int t = et[a];
+        for (int k = 0; k < NF[t]; ++k) {
+            std::set<int32_t> face;
+            for (int q = 0; q < FS[t]; ++q) face.insert(en[a][FACES[t][k][q]]);
+            if ((int)face.size() < FS[t]) continue;  // repeated node: no face
+            bool all = true;
+            for (int32_t v : face)
+                if (std::find(en[b].begin(), en[b].end(), v) == en[b].end()) all = false;
+            if (all) return true;
+        }
+        return false;
+    };
+    const int64_t rows = sample ? n_sample : n_elems;
+    std::vector<std::set<int32_t>> adj(rows);
+    for (int64_t i = 0; i < rows; ++i) {
+        const int64_t e = sample ? sample[i] : i;
+        if (e < 0 || e >= n_elems || et[e] < 0) continue;
+        for (int32_t v : en[e])
+            for (int32_t f : ne[v])
+                if (f != e && (face_in(e, f) || face_in(f, e))) adj[i].insert(f);
+    }
+    emit(adj, r->elem_row_ptr, r->elem_col);
+    return r;
+}
+
 }  // extern "C"
