@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--elem-adj", action="store_true",
+                    help="also time element face adjacency from the built node -> element CSR")
     ap.add_argument("--tune", choices=["auto", "off", "sweep"], default="auto",
                     help="launch tuning: cached or timed once (auto), planner default (off), re-timed (sweep)")
     ap.add_argument("--requests", type=int, default=10000, help="serve workload: number of requests")
@@ -434,6 +436,10 @@ def main():
     if not args.no_e2e:
         e2e = end_to_end(torch, nn, b, mesh, dm, want, ws, ws_bytes, out, args.steps, dev, world)
 
+    adjacency = None
+    if args.elem_adj and "elems" in out:
+        adjacency = time_adjacency(torch, nn, b, dm, out, flush, stream, max(args.steps // 2, 3))
+
     baseline = None
     if rank == 0 and world == 1 and not args.no_baseline:
         baseline = oracle_baseline()
@@ -463,6 +469,8 @@ def main():
         "e2e": e2e,
         "cpu_baseline": baseline,
     }
+    if adjacency is not None:
+        line["element_adjacency"] = adjacency
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -509,6 +517,34 @@ def end_to_end(torch, nn, b, mesh, dm, want, ws, ws_bytes, out, steps, dev, worl
     return {"value": world * mesh.n_elems * steps / dt / 1e6, "unit": "Melem/s",
             "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
             "ms_per_step": dt * 1e3 / steps}
+
+
+def time_adjacency(torch, nn, b, dm, out, flush, stream, steps):
+    """Element face adjacency from the node -> element CSR just built: CUDA-event time per call, L2 flushed."""
+    rp_e, col_e = out["elems"]
+    node_elems = (rp_e, col_e)
+    rp, col = b.element_neighbors(dm, node_elems)          # sizes the output, checks the status
+    ws_bytes, _ = nn.nn_element_neighbors_query(b.h, dm.struct())
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=rp.device)
+    col_full = torch.empty(max(col.numel(), 1), dtype=torch.int32, device=rp.device)
+    ne = nn.NNCSR(rp_e.data_ptr(), col_e.data_ptr(), col_e.numel())
+    dst = nn.NNCSR(rp.data_ptr(), col_full.data_ptr(), col_full.numel())
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = nn.nn_element_neighbors(b.h, dm.struct(), ne, dst, ws.data_ptr(), ws_bytes, b.status.data_ptr(),
+                                     stream.cuda_stream)
+        e1.record(stream)
+        if st:
+            raise nn.NNError(st, "nn_element_neighbors")
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    assert int(b.status.item()) == 0
+    ms = sorted(times)[len(times) // 2]
+    return {"ms_median": ms, "melem_per_s": dm.n_elems / (ms * 1e-3) / 1e6, "nnz": int(col.numel()),
+            "gpu_launches_per_call": 3, "steps": steps}
 
 
 def max_over_ranks(x, world, device):

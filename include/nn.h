@@ -120,6 +120,25 @@ typedef struct {
 } nn_tuning;
 nn_status nn_set_tuning(nn_handle* h, const nn_tuning* tuning);
 
+/* Element face adjacency (the neighbours "for each element" that Sec. 1
+ * lists beside the per-node ones; the paper works out only the latter).
+ * Two distinct elements are face neighbours when every node of some face of
+ * one of them belongs to the other.  Faces are tri and quad edges, tet
+ * triangles and hex quads (VTK order); a face with a repeated node is no
+ * face.  For a conforming mesh this is the dual graph; a hex face split into
+ * two tet triangles borders both tets.
+ * node_elems: the mesh's node -> element CSR on the device (as built by
+ * nn_neighbor_elements or nn_neighbors_both; col_capacity is not used).
+ * out: row_ptr [n_elems+1] int64 and col, rows ascending; NN_ERR_CAPACITY on
+ * the device if col_capacity is too small (nn_element_neighbors_query gives
+ * a bound that holds when every face borders at most two elements of each
+ * side).  Workspace: nn_element_neighbors_query.  Asynchronous on stream;
+ * elements with invalid nodes or offsets are skipped (the neighbour build
+ * reports them). */
+nn_status nn_element_neighbors_query(nn_handle* h, const nn_mesh* mesh, size_t* ws_bytes, int64_t* col_cap);
+nn_status nn_element_neighbors(nn_handle* h, const nn_mesh* mesh, const nn_csr* node_elems, nn_csr* out,
+                               void* ws, size_t ws_bytes, int32_t* d_status, nn_stream_t stream);
+
 /* Parameters of the build plan for a mesh (host-only; for tooling and
  * traffic accounting).  Fills up to n of: info[0] bucket shift (a bucket is
  * 2^info[0] consecutive node ids), [1] number of buckets, [2] CTAs of the

@@ -692,6 +692,55 @@ nn_status nn_plan_info(nn_handle* h, const nn_mesh* mesh, int want, int64_t* inf
     return NN_OK;
 }
 
+nn_status nn_element_neighbors_query(nn_handle* h, const nn_mesh* mesh, size_t* ws_bytes, int64_t* col_cap) {
+    if (!h) return NN_ERR_ARG;
+    nn_status st = check_mesh(mesh);
+    if (st != NN_OK) return st;
+    const size_t T = (size_t)mesh->n_elems;
+    if (ws_bytes) *ws_bytes = align_up(T * 4) + align_up((adjacency_scan_tiles((int64_t)T) + 1) * 8) + ALIGN;
+    // faces per element (6 at most) times two
+    if (col_cap) *col_cap = (int64_t)T * (mesh->type == NN_TRI ? 6 : mesh->type == NN_HEX || mesh->type == NN_MIXED ? 12 : 8);
+    return NN_OK;
+}
+
+nn_status nn_element_neighbors(nn_handle* h, const nn_mesh* mesh, const nn_csr* node_elems, nn_csr* out, void* ws,
+                               size_t ws_bytes, int32_t* d_status, nn_stream_t stream) {
+    if (!h || !node_elems || !node_elems->row_ptr || !out || !out->row_ptr || !d_status) return NN_ERR_ARG;
+    nn_status st = check_mesh(mesh);
+    if (st != NN_OK) return st;
+    if (out->col_capacity < 0 || (out->col_capacity > 0 && !out->col)) return NN_ERR_ARG;
+    if (mesh->n_conn > 0 && !node_elems->col) return NN_ERR_ARG;
+    size_t need = 0;
+    nn_element_neighbors_query(h, mesh, &need, nullptr);
+    if (ws_bytes < need || !ws || (reinterpret_cast<uintptr_t>(ws) & (ALIGN - 1))) return NN_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t* w = static_cast<uint8_t*>(ws);
+    const size_t T = (size_t)mesh->n_elems;
+    const size_t off_lb = align_up(T * 4), off_ticket = off_lb + align_up((adjacency_scan_tiles((int64_t)T) + 1) * 8);
+    if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return NN_ERR_CUDA;
+    if (cudaMemsetAsync(w + off_lb, 0, off_ticket + ALIGN - off_lb, s) != cudaSuccess) return NN_ERR_CUDA;
+    if (T == 0) return cudaMemsetAsync(out->row_ptr, 0, 8, s) == cudaSuccess ? NN_OK : NN_ERR_CUDA;
+    AdjParams p{};
+    p.type = mesh->type;
+    p.n_nodes = mesh->n_nodes;
+    p.n_elems = mesh->n_elems;
+    p.n_conn = mesh->n_conn;
+    p.conn = mesh->conn;
+    p.elem_ptr = mesh->elem_ptr;
+    p.elem_type = mesh->elem_type;
+    p.ne_rp = node_elems->row_ptr;
+    p.ne_col = node_elems->col;
+    p.cnt = reinterpret_cast<uint32_t*>(w);
+    p.lb_state = reinterpret_cast<uint64_t*>(w + off_lb);
+    p.ticket = reinterpret_cast<uint32_t*>(w + off_ticket);
+    p.rp = out->row_ptr;
+    p.col = out->col;
+    p.cap = out->col_capacity;
+    p.status = d_status;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sms * 8, ((int64_t)T + 255) / 256));
+    return launch_adjacency(p, grid, s) == cudaSuccess ? NN_OK : NN_ERR_CUDA;
+}
+
 nn_status nn_set_tuning(nn_handle* h, const nn_tuning* t) {
     if (!h) return NN_ERR_ARG;
     if (!t) {

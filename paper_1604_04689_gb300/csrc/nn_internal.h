@@ -159,7 +159,25 @@ struct CompactParams {
     BatchTables batch;
 };
 
+// Element face adjacency (nn_adj.cu).
+struct AdjParams {
+    int type;
+    int64_t n_nodes, n_elems, n_conn;
+    const int32_t* conn;
+    const int64_t* elem_ptr;
+    const uint8_t* elem_type;
+    const int64_t* ne_rp;    // node -> element CSR
+    const int32_t* ne_col;
+    uint32_t* cnt;           // [n_elems] neighbours per element
+    uint64_t* lb_state;      // lookback words, one per tile of elements
+    uint32_t* ticket;
+    int64_t* rp; int32_t* col; int64_t cap;
+    int32_t* status;
+};
+
 // launchers (return the CUDA error of the launch)
+cudaError_t launch_adjacency(const AdjParams& p, int grid, cudaStream_t s);
+size_t adjacency_scan_tiles(int64_t n_elems);
 cudaError_t launch_node_compact(const CompactParams& p, int copy_grid, cudaStream_t s);
 cudaError_t launch_hist(const EmitParams& p, size_t smem, cudaStream_t s);
 cudaError_t launch_part(const EmitParams& p, cudaStream_t s);

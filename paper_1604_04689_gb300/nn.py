@@ -86,6 +86,12 @@ def lib():
             L.nn_profile_enable.restype = C.c_int
             L.nn_profile_read.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]
             L.nn_profile_read.restype = C.c_int
+            L.nn_element_neighbors_query.argtypes = [P, C.POINTER(NNMesh), C.POINTER(C.c_size_t),
+                                                     C.POINTER(C.c_int64)]
+            L.nn_element_neighbors_query.restype = C.c_int
+            L.nn_element_neighbors.argtypes = [P, C.POINTER(NNMesh), C.POINTER(NNCSR), C.POINTER(NNCSR), P,
+                                               C.c_size_t, P, P]
+            L.nn_element_neighbors.restype = C.c_int
             L.nn_set_tuning.argtypes = [P, C.POINTER(NNTuning)]
             L.nn_set_tuning.restype = C.c_int
             L.nn_plan_info.argtypes = [P, C.POINTER(NNMesh), C.c_int, C.POINTER(C.c_int64), C.c_int]
@@ -167,6 +173,22 @@ def nn_neighbors_both(h, mesh: NNMesh, nodes: NNCSR, elems: NNCSR, ws: int, ws_b
                       stream: int) -> int:
     return lib().nn_neighbors_both(h, C.byref(mesh), C.byref(nodes), C.byref(elems), ws, ws_bytes, d_status,
                                    stream)
+
+
+def nn_element_neighbors_query(h: int, mesh: NNMesh):
+    """(workspace bytes, col capacity bound) for element face adjacency."""
+    ws = C.c_size_t()
+    cap = C.c_int64()
+    st = lib().nn_element_neighbors_query(h, C.byref(mesh), C.byref(ws), C.byref(cap))
+    if st:
+        raise NNError(st, "nn_element_neighbors_query")
+    return ws.value, cap.value
+
+
+def nn_element_neighbors(h, mesh: NNMesh, node_elems: NNCSR, out: NNCSR, ws: int, ws_bytes: int, d_status: int,
+                         stream: int) -> int:
+    return lib().nn_element_neighbors(h, C.byref(mesh), C.byref(node_elems), C.byref(out), ws, ws_bytes, d_status,
+                                      stream)
 
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -358,6 +380,37 @@ class Builder:
         if want == WANT_ELEMS:
             return nn_neighbor_elements(self.h, mesh, csr(out["elems"]), ws.data_ptr(), ws_bytes, sp, s)
         return nn_neighbors_both(self.h, mesh, csr(out["nodes"]), csr(out["elems"]), ws.data_ptr(), ws_bytes, sp, s)
+
+    def element_neighbors(self, dm: DeviceMesh, node_elems, stream=None, sync: bool = True):
+        """Face neighbours of every element: (row_ptr, col) on the device, from
+        the mesh's node -> element CSR ``node_elems`` = (row_ptr, col).  With
+        ``sync``, waits, checks the device status and trims col."""
+        torch = self.torch
+        ws_bytes, cap = nn_element_neighbors_query(self.h, dm.struct())
+        ws = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=self.device)
+        rp = torch.empty(dm.n_elems + 1, dtype=torch.int64, device=self.device)
+        s = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        ne_rp, ne_col = node_elems
+        for attempt in range(2):
+            col = torch.empty(max(cap, 1), dtype=torch.int32, device=self.device)
+            st = nn_element_neighbors(self.h, dm.struct(),
+                                      NNCSR(ne_rp.data_ptr(), ne_col.data_ptr(), ne_col.numel()),
+                                      NNCSR(rp.data_ptr(), col.data_ptr(), col.numel()), ws.data_ptr(), ws_bytes,
+                                      self.status.data_ptr(), s)
+            if st:
+                raise NNError(st, "nn_element_neighbors")
+            self._adj_keep = ws
+            if not sync:
+                return rp, col
+            torch.cuda.synchronize(self.device)
+            status = int(self.status.item())
+            if status == 3 and attempt == 0:   # faces shared by many elements: the exact size is in rp[-1]
+                cap = int(rp[-1].item())
+                continue
+            if status:
+                raise NNError(status, "nn_element_neighbors (device)")
+            break
+        return rp, col[: int(rp[-1].item())]
 
     def build(self, dm: DeviceMesh, want: int = WANT_BOTH):
         """Build and return {'status': int, 'nodes': (row_ptr, col), 'elems': (row_ptr, col)} (col trimmed)."""
