@@ -8,11 +8,11 @@
 // conforming mesh this is the dual graph; a hex face split into two tet
 // triangles borders both tets.
 //
-// One thread per element e walks the element rows of e's distinct nodes.  A
-// candidate f is considered at the first node of e that it contains (so once),
-// its nodes are gathered, and the two face tests decide.  Three kernels:
-// count, exclusive scan (decoupled lookback over tiles of elements), and
-// write followed by an in-place sort of the (short) row.
+// One thread per element merges the (sorted) element rows of its distinct
+// nodes, which yields every element sharing a node with it once, in
+// ascending order, with the number of shared nodes; the face tests run only
+// where that number allows a shared face.  Three kernels: count, exclusive
+// scan (decoupled lookback over tiles of elements), and write.
 #include "nn_device.cuh"
 
 namespace nn {
@@ -73,30 +73,53 @@ __device__ __forceinline__ bool face_in(int ta, const int32_t* na, const int32_t
     return false;
 }
 
-// Calls emit(f) for every face neighbour f of element e (each once).
+// Calls emit(f) for every face neighbour f of element e, once each, in
+// ascending order.  The element rows of e's distinct nodes are sorted, so a
+// k-way merge of them visits every element sharing a node with e once and
+// counts the nodes they share; only an element sharing at least as many nodes
+// as the smallest face that could join them has its nodes gathered and the
+// face tests run (a tet sees ~96 row entries but ~4 such candidates).
 template <class F>
 __device__ __forceinline__ void for_each_neighbour(const AdjParams& p, int64_t e, F&& emit) {
+    constexpr int32_t END = 0x7fffffff;
     int32_t nd[8];
     const int t = load_element(p, e, nd);
     if (t < 0) return;
     const int n = npe_of(t);
-    for (int i = 0; i < n; ++i) {
-        const int32_t v = nd[i];
-        bool rep = false;
-        for (int j = 0; j < i; ++j) rep |= nd[j] == v;
-        if (rep) continue;
-        for (int64_t r = p.ne_rp[v], r1 = p.ne_rp[v + 1]; r < r1; ++r) {
-            const int32_t f = p.ne_col[r];
-            if ((int64_t)f == e || f < 0 || (int64_t)f >= p.n_elems) continue;
-            int32_t fd[8];
-            const int tf = load_element(p, f, fd);
-            if (tf < 0) continue;
-            const int nf = npe_of(tf);
-            bool earlier = false;  // f contains a distinct earlier node of e: counted there
-            for (int j = 0; j < i && !earlier; ++j) earlier = nd[j] != v && contains(fd, nf, nd[j]);
-            if (earlier) continue;
-            if (face_in(t, nd, fd, nf) || face_in(tf, fd, nd, n)) emit(f);
+    // one row per node slot (a repeated node, or a slot past the element, gets an empty one)
+    int64_t pos[8], end[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        bool use = i < n;
+#pragma unroll
+        for (int j = 0; j < i; ++j) use = use && !(j < n && nd[j] == nd[i]);
+        pos[i] = use ? p.ne_rp[nd[i]] : 0;
+        end[i] = use ? p.ne_rp[nd[i] + 1] : 0;
+    }
+    int32_t head[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) head[i] = pos[i] < end[i] ? p.ne_col[pos[i]] : END;
+    // any face of e, and any face of a neighbour of another type (2-node faces in a mixed mesh)
+    const int dmin = p.type == NN_MIXED ? 2 : c_fsize[t];
+    for (;;) {
+        int32_t m = END;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) m = min(m, head[j]);
+        if (m == END) break;
+        int shared = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (head[j] == m) {
+                ++shared;
+                ++pos[j];
+                head[j] = pos[j] < end[j] ? p.ne_col[pos[j]] : END;
+            }
         }
+        if ((int64_t)m == e || shared < dmin || m < 0 || (int64_t)m >= p.n_elems) continue;
+        int32_t fd[8];
+        const int tf = load_element(p, m, fd);
+        if (tf < 0) continue;
+        if (face_in(t, nd, fd, npe_of(tf)) || face_in(tf, fd, nd, n)) emit(m);
     }
 }
 
@@ -143,7 +166,6 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_write(AdjParams p) {
             if (k < n) row[k] = f;
             ++k;
         });
-        insertion_sort(reinterpret_cast<uint32_t*>(row), (int)n);  // ids >= 0: unsigned order is signed order
     }
 }
 
