@@ -57,7 +57,7 @@ struct Plan {
     int G_fine = 1;
     size_t emit_smem = 0;
     size_t off_estart = 0, off_nfc = 0, off_ntmp = 0, off_ubk = 0, off_nloc = 0, off_nstart = 0, off_lb_ns = 0;
-    size_t off_hist = 0, off_bstart = 0, off_gcur = 0, off_gcur_c = 0, off_rec_tmp = 0, off_rec = 0, off_lb_off = 0, off_lb_n = 0, off_lb_e = 0,
+    size_t off_hist = 0, off_bstart = 0, off_gcur = 0, off_gcur_c = 0, off_rec_tmp = 0, off_rec = 0, off_lb_off = 0,
            off_ctrl = 0, off_spill = 0, zero_begin = 0, zero_end = 0;
     size_t ws_min = 0, ws_rec = 0;
     int bucket_grid = 0;
@@ -201,8 +201,6 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     p.off_nfc = o; o = align_up(o + ((want & NN_WANT_ELEMS) ? (size_t)p.B * 4 : 0));
     p.off_lb_off = o; o = align_up(o + (size_t)((p.B + OFFSETS_THREADS - 1) / OFFSETS_THREADS) * 8 + 8);
     p.off_lb_ns = o; o = align_up(o + (wn ? (size_t)((p.B + 127) / 128) * 8 + 8 : 0));
-    p.off_lb_n = o; o = align_up(o + ((want & NN_WANT_NODES) ? (size_t)p.B * 8 : 0));
-    p.off_lb_e = o; o = align_up(o + ((want & NN_WANT_ELEMS) ? (size_t)p.B * 8 : 0));
     p.off_ctrl = o; o = align_up(o + 64);
     p.zero_end = o;
     p.off_spill = o;
@@ -300,8 +298,6 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
     bp.rec = ep.rec;
     bp.bstart = op.bstart;
     bp.estart = op.estart;
-    bp.lb_n = reinterpret_cast<uint64_t*>(w + p.off_lb_n);
-    bp.lb_e = reinterpret_cast<uint64_t*>(w + p.off_lb_e);
     bp.ticket = ctrl + 1;
     bp.spill_cursor = reinterpret_cast<unsigned long long*>(ctrl + 2);
     bp.spill = reinterpret_cast<uint32_t*>(w + p.off_spill);
@@ -370,8 +366,7 @@ struct BatchPlan {
     int sb = 7;
     int64_t B_cap = 0;
     size_t hdr_bytes = 0, meshes_off = 0, elem_off_off = 0, bucket_off_off = 0, table_bytes = 0;
-    size_t off_bcount = 0, off_bstart = 0, off_gcur = 0, off_rec = 0, off_lb_off = 0, off_lb_n = 0,
-           off_lb_e = 0, off_ctrl = 0, off_spill = 0, ws_min = 0, ws_rec = 0, off_nfc = 0,
+    size_t off_bcount = 0, off_bstart = 0, off_gcur = 0, off_rec = 0, off_lb_off = 0, off_ctrl = 0, off_spill = 0, ws_min = 0, ws_rec = 0, off_nfc = 0,
            off_estart = 0, off_ntmp = 0, off_ubk = 0, off_nloc = 0, off_nstart = 0, off_lb_ns = 0;
     size_t bucket_smem = 0;
     uint32_t area_words = 0;
@@ -419,8 +414,6 @@ nn_status batch_plan(const nn_handle* h, const nn_batch_caps* c, BatchPlan* out)
     p.off_lb_ns = o; o = align_up(o + (wn ? (size_t)((p.B_cap + 127) / 128) * 8 + 8 : 0));
     p.tiles_cap = (p.B_cap + OFFSETS_THREADS - 1) / OFFSETS_THREADS;
     p.off_lb_off = o; o = align_up(o + ((size_t)p.tiles_cap + 1) * 8);
-    p.off_lb_n = o; o = align_up(o + (size_t)p.B_cap * 8);
-    p.off_lb_e = o; o = align_up(o + (size_t)p.B_cap * 8);
     p.off_ctrl = o; o = align_up(o + 64);
     p.off_spill = o;
     p.ws_min = o;
@@ -522,13 +515,11 @@ nn_status batch_launch(nn_handle* h, const nn_batch_caps* c, const void* staging
     uint32_t* gcur = reinterpret_cast<uint32_t*>(w + bp.off_gcur);
     uint32_t* ctrl = reinterpret_cast<uint32_t*>(w + bp.off_ctrl);
     uint64_t* lb_off = reinterpret_cast<uint64_t*>(w + bp.off_lb_off);
-    uint64_t* lb_n = reinterpret_cast<uint64_t*>(w + bp.off_lb_n);
-    uint64_t* lb_e = reinterpret_cast<uint64_t*>(w + bp.off_lb_e);
     uint8_t* rec = w + bp.off_rec;
-    if (launch_batch_emit(bt, bcount, nfc, gcur, rec, lb_off, lb_n, lb_e, ctrl, bp.emit_grid, 0, s,
+    if (launch_batch_emit(bt, bcount, nfc, gcur, rec, lb_off, ctrl, bp.emit_grid, 0, s,
                           reinterpret_cast<uint64_t*>(w + bp.off_lb_ns)) != cudaSuccess)
         return NN_ERR_CUDA;
-    if (launch_batch_emit(bt, bcount, nfc, gcur, rec, lb_off, lb_n, lb_e, ctrl, bp.emit_grid, 1, s) != cudaSuccess)
+    if (launch_batch_emit(bt, bcount, nfc, gcur, rec, lb_off, ctrl, bp.emit_grid, 1, s) != cudaSuccess)
         return NN_ERR_CUDA;
     OffsetsParams op{};
     op.hist = bcount;
@@ -544,15 +535,13 @@ nn_status batch_launch(nn_handle* h, const nn_batch_caps* c, const void* staging
     op.status = reinterpret_cast<int32_t*>(ctrl + 8);  // passed on to every mesh by the bucket pass
     op.hdr = bt.hdr;
     if (launch_offsets(op, s) != cudaSuccess) return NN_ERR_CUDA;
-    if (launch_batch_emit(bt, bcount, nfc, gcur, rec, lb_off, lb_n, lb_e, ctrl, bp.emit_grid, 2, s) != cudaSuccess)
+    if (launch_batch_emit(bt, bcount, nfc, gcur, rec, lb_off, ctrl, bp.emit_grid, 2, s) != cudaSuccess)
         return NN_ERR_CUDA;
     BucketParams kp{};
     kp.n_buckets = 0;
     kp.rec = rec;
     kp.bstart = op.bstart;
     kp.estart = op.estart;
-    kp.lb_n = lb_n;
-    kp.lb_e = lb_e;
     kp.ticket = ctrl + 1;
     kp.spill_cursor = reinterpret_cast<unsigned long long*>(ctrl + 2);
     kp.spill = reinterpret_cast<uint32_t*>(w + bp.off_spill);

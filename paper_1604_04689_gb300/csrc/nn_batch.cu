@@ -92,8 +92,7 @@ __device__ __forceinline__ void walk_batch(const BatchTables& bt, F&& f) {
 }
 
 __global__ void __launch_bounds__(BATCH_THREADS) k_batch_init(BatchTables bt, uint32_t* bcount, uint32_t* nfc,
-                                                              uint64_t* lb_off, uint64_t* lb_n,
-                                                              uint64_t* lb_e, uint32_t* ctrl, uint64_t* lb_ns) {
+                                                              uint64_t* lb_off, uint32_t* ctrl, uint64_t* lb_ns) {
     const int64_t B = bt.hdr->n_buckets;
     const int64_t tiles = (B + OFFSETS_THREADS - 1) / OFFSETS_THREADS;
     const int n = bt.hdr->n_meshes;
@@ -101,8 +100,6 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch_init(BatchTables bt, ui
     for (int64_t i = i0; i < B; i += st) {
         bcount[i] = 0;
         nfc[i] = 0;
-        lb_n[i] = 0;
-        lb_e[i] = 0;
     }
     for (int64_t i = i0; i < tiles + 1; i += st) lb_off[i] = 0;
     if (lb_ns)
@@ -176,9 +173,9 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_part_b(BatchTables bt, uint32
 }  // namespace
 
 cudaError_t launch_batch_emit(const BatchTables& bt, uint32_t* bcount, uint32_t* nfc, uint32_t* gcur, uint8_t* rec,
-                              uint64_t* lb_off, uint64_t* lb_n, uint64_t* lb_e, uint32_t* ctrl, int grid,
-                              int stage, cudaStream_t s, uint64_t* lb_ns) {
-    if (stage == 0) k_batch_init<<<grid, BATCH_THREADS, 0, s>>>(bt, bcount, nfc, lb_off, lb_n, lb_e, ctrl, lb_ns);
+                              uint64_t* lb_off, uint32_t* ctrl, int grid, int stage, cudaStream_t s,
+                              uint64_t* lb_ns) {
+    if (stage == 0) k_batch_init<<<grid, BATCH_THREADS, 0, s>>>(bt, bcount, nfc, lb_off, ctrl, lb_ns);
     else if (stage == 1) k_hist_b<<<grid, BATCH_THREADS, 0, s>>>(bt, bcount, nfc);
     else k_part_b<<<grid, BATCH_THREADS, 0, s>>>(bt, gcur, rec);
     return cudaGetLastError();

@@ -287,7 +287,6 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_bucket(BucketParams 
             }
             misc[2] = base;
             misc[4] = flags;
-            if (want_e && !p.estart) lb_publish(p.lb_e, b, Eb, first);
         }
         __syncthreads();
         const uint32_t flags = (uint32_t)misc[4];
@@ -298,16 +297,11 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_bucket(BucketParams 
         const uint64_t ucap = insm ? (uint64_t)p.area_words - R - Eb : (uint64_t)p.area_words;
 
         // the element rows' offset: a prefix of the record counts, known
-        // before this pass (for a batch, relative to the mesh's first bucket);
-        // without it, a lookback over the buckets that warp 0 resolves while
-        // the others group records
-        if (warp == 0 && want_e) {
-            const uint64_t ge = p.estart ? (uint64_t)(p.estart[b] - p.estart[first])
-                                         : lb_resolve_wide<4>(p.lb_e, b, Eb, status, first);
-            if (lane == 0) {
-                misc[1] = ge;
-                if (ge + Eb > (uint64_t)sh_out.cap_e) set_status(status, NN_ERR_CAPACITY);
-            }
+        // before this pass (for a batch, relative to the mesh's first bucket)
+        if (want_e && tid == 0) {
+            const uint64_t ge = (uint64_t)(p.estart[b] - p.estart[first]);
+            misc[1] = ge;
+            if (ge + Eb > (uint64_t)sh_out.cap_e) set_status(status, NN_ERR_CAPACITY);
         }
         // 2. record indices grouped by node (a node with more than 2^21
         // records in one bucket cannot be stashed: any slot that large is

@@ -1,6 +1,5 @@
 // Device helpers shared by the libnn kernels: status reporting, bounded
-// decoupled lookback, block scans, record packing, element edge tables and
-// row sorting.
+// decoupled lookback, block scans, record packing and element edge tables.
 #pragma once
 
 #include <cstdint>
@@ -21,14 +20,6 @@ __device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-// Relaxed load: for lookback words, which carry their flag and value in one
-// 64-bit word (nothing else is read on the strength of the flag), so several
-// can be in flight at once.
-__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
-    uint64_t v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
 __device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -46,39 +37,6 @@ __device__ __forceinline__ uint64_t global_ns() {
 constexpr uint64_t LB_AGG = 1ull << 62;
 constexpr uint64_t LB_INC = 2ull << 62;
 constexpr uint64_t LB_VAL = (1ull << 62) - 1;
-
-// Called by ONE thread; returns the exclusive prefix of tile t.
-__device__ inline uint64_t lookback(uint64_t* state, uint64_t t, uint64_t agg, int32_t* status) {
-    if (t == 0) {
-        st_release(&state[0], LB_INC | agg);
-        return 0;
-    }
-    st_release(&state[t], LB_AGG | agg);
-    uint64_t excl = 0;
-    int64_t p = (int64_t)t - 1;
-    uint64_t t0 = 0;
-    while (p >= 0) {
-        uint64_t s = ld_acquire(&state[p]);
-        uint64_t flag = s >> 62;
-        if (flag == 0) {
-            uint64_t now = global_ns();
-            if (t0 == 0) {
-                t0 = now;
-            } else if (now - t0 > WAIT_LIMIT_NS) {
-                set_status(status, NN_ERR_TIMEOUT);
-                break;
-            }
-            __nanosleep(64);
-            continue;
-        }
-        t0 = 0;
-        excl += s & LB_VAL;
-        if (flag == 2) break;
-        --p;
-    }
-    st_release(&state[t], LB_INC | ((excl + agg) & LB_VAL));
-    return excl;
-}
 
 // Warp-parallel lookback in two halves.  lb_publish (one thread) makes the
 // tile's aggregate visible as soon as it is known; lb_resolve (all 32 lanes
@@ -114,71 +72,6 @@ __device__ inline uint64_t lb_resolve(uint64_t* state, uint64_t t, uint64_t agg,
         if (inc) break;
         p -= k;
         if (k == 0) {  // nearest predecessor not ready yet: bounded wait
-            const uint64_t now = global_ns();
-            if (t0 == 0) {
-                t0 = now;
-            } else if (now - t0 > WAIT_LIMIT_NS) {
-                if (lane == 0) set_status(status, NN_ERR_TIMEOUT);
-                break;
-            }
-            __nanosleep(100);
-        } else {
-            t0 = 0;
-        }
-    }
-    if (lane == 0) st_release(&state[t], LB_INC | ((excl + agg) & LB_VAL));
-    __syncwarp();
-    return excl;
-}
-
-// As lb_resolve, but every lane reads V consecutive predecessors per step
-// (32 V per step): when hundreds of tiles are in flight, the nearest
-// inclusive prefix is that far back, and each step is an L2 round trip.
-// Non-blocking (blocking = false): gives up, publishing nothing, at the first
-// predecessor that is not ready, and reports *ok = false.
-template <int V>
-__device__ inline uint64_t lb_resolve_wide(uint64_t* state, uint64_t t, uint64_t agg, int32_t* status,
-                                           uint64_t first = 0, bool blocking = true, bool* ok = nullptr) {
-    const int lane = threadIdx.x & 31;
-    if (ok) *ok = true;
-    if (t == first) return 0;
-    uint64_t excl = 0;
-    int64_t p = (int64_t)t - 1;  // nearest predecessor not yet consumed
-    uint64_t t0 = 0;
-    for (;;) {
-        uint64_t s[V];
-        int nr = V, inc = V;  // first not-ready / first inclusive among this lane's V (nearest first)
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-            const int64_t idx = p - (int64_t)lane * V - j;
-            s[j] = idx >= (int64_t)first ? ld_relaxed(&state[idx]) : LB_INC;  // before the chain: zero
-        }
-#pragma unroll
-        for (int j = V - 1; j >= 0; --j) {
-            if ((s[j] >> 62) == 0) nr = j;
-            if ((s[j] >> 62) == 2) inc = j;
-        }
-        const unsigned nr_lanes = __ballot_sync(0xffffffffu, nr < V);
-        const unsigned inc_lanes = __ballot_sync(0xffffffffu, inc < V);
-        const int l_nr = nr_lanes ? __ffs(nr_lanes) - 1 : 32, l_inc = inc_lanes ? __ffs(inc_lanes) - 1 : 32;
-        const int k_nr = l_nr < 32 ? l_nr * V + __shfl_sync(0xffffffffu, nr, l_nr & 31) : 32 * V;
-        const int k_inc = l_inc < 32 ? l_inc * V + __shfl_sync(0xffffffffu, inc, l_inc & 31) : 32 * V;
-        const bool done = k_inc < k_nr;  // an inclusive prefix before any gap: consume through it
-        const int lim = done ? k_inc + 1 : k_nr;
-        uint64_t v = 0;
-#pragma unroll
-        for (int j = 0; j < V; ++j)
-            if (lane * V + j < lim) v += s[j] & LB_VAL;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-        excl += v;
-        if (done) break;
-        p -= k_nr;
-        if (k_nr == 0) {  // nearest predecessor not ready yet: bounded wait
-            if (!blocking) {
-                if (ok) *ok = false;
-                return 0;
-            }
             const uint64_t now = global_ns();
             if (t0 == 0) {
                 t0 = now;
@@ -309,46 +202,5 @@ __device__ __forceinline__ int nbr_of(int t, int i, int s) {
     }
 }
 __device__ __forceinline__ int k_of(int t) { return (t == NN_TRI || t == NN_QUAD) ? 2 : 3; }
-
-// ----------------------------------------------------------------- sorting
-// Insertion sort of a short row (generic pointer: shared or global memory).
-__device__ inline void insertion_sort(uint32_t* a, int n) {
-    for (int i = 1; i < n; ++i) {
-        uint32_t x = a[i];
-        int j = i - 1;
-        while (j >= 0 && a[j] > x) {
-            a[j + 1] = a[j];
-            --j;
-        }
-        a[j + 1] = x;
-    }
-}
-
-// Ascending bitonic sort of a[0..n) by the whole block (generic pointer).
-// Uses the formulation in which every compare-exchange puts the minimum at
-// the lower index (first step of each merge mirrors the block), so indices
-// >= n behave as +infinity and their compare-exchanges can be skipped.
-// All threads of the block must call.
-__device__ inline void block_bitonic_sort(uint32_t* a, int64_t n) {
-    if (n < 2) return;
-    int64_t P = 1;
-    while (P < n) P <<= 1;
-    for (int64_t k = 2; k <= P; k <<= 1) {
-        for (int64_t j = k >> 1; j > 0; j >>= 1) {
-            for (int64_t t = threadIdx.x; t < (P >> 1); t += blockDim.x) {
-                int64_t idx = ((t & ~(j - 1)) << 1) | (t & (j - 1));
-                int64_t q = (j == (k >> 1)) ? (idx ^ (k - 1)) : (idx ^ j);
-                if (q < n) {
-                    uint32_t x = a[idx], y = a[q];
-                    if (x > y) {
-                        a[idx] = y;
-                        a[q] = x;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
 
 }  // namespace nn

@@ -117,9 +117,7 @@ struct BucketParams {
     int64_t n_buckets;
     const uint8_t* rec;
     const uint32_t* bstart;
-    const uint32_t* estart; // element-CSR offset of each bucket, batch-wide (nullptr: found by lookback in lb_e)
-    uint64_t* lb_n;         // lookback words, node CSR, one per bucket
-    uint64_t* lb_e;         // lookback words, element CSR, one per bucket
+    const uint32_t* estart; // element-CSR offset of each bucket, batch-wide (required when element rows are wanted)
     uint32_t* ticket;
     uint32_t* spill;        // global scratch for buckets too large for shared memory
     uint64_t spill_words;
@@ -187,8 +185,8 @@ cudaError_t launch_bucket(const BucketParams& p, int grid, int threads, size_t s
 size_t bucket_fixed_bytes(int sb, int threads, int wide);  // shared memory of the bucket kernel outside its area
 cudaError_t bucket_occupancy(int* blocks, int threads, int wide, size_t smem);
 cudaError_t launch_batch_emit(const BatchTables& bt, uint32_t* bcount, uint32_t* nfc, uint32_t* gcur, uint8_t* rec,
-                              uint64_t* lb_off, uint64_t* lb_n, uint64_t* lb_e, uint32_t* ctrl, int grid,
-                              int stage, cudaStream_t s, uint64_t* lb_ns = nullptr);
+                              uint64_t* lb_off, uint32_t* ctrl, int grid, int stage, cudaStream_t s,
+                              uint64_t* lb_ns = nullptr);
 int batch_threads();
 cudaError_t set_emit_smem_all(size_t bytes);
 cudaError_t set_bucket_smem_all(size_t bytes);
