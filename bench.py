@@ -478,45 +478,74 @@ def main():
 
 
 def end_to_end(torch, nn, b, mesh, dm, want, ws, ws_bytes, out, steps, dev, world):
-    """Same metric through the C ABI with host buffers: every step copies the
-    connectivity host->device from pinned memory, builds, and copies both CSRs
-    device->host into pinned memory (row pointers, then the used part of col)."""
+    """Same metric through the C ABI with host buffers.  Every step copies its
+    connectivity host -> device from pinned memory, builds, and copies both
+    CSRs device -> host into pinned memory (row pointers, then the used part of
+    col).  Steps are pipelined the way a host-fed service runs them: uploads on
+    one stream, builds on another, downloads on a third, two buffer sets, and
+    the column downloads of step i enqueued once its row pointers (and so its
+    sizes) have arrived, while step i + 1 uploads and builds."""
+    sA = torch.cuda.current_stream(dev)            # builds
+    sU, sD = torch.cuda.Stream(dev), torch.cuda.Stream(dev)   # uploads, downloads
     h_conn = torch.from_numpy(mesh.conn).pin_memory()
-    d_conn = torch.empty_like(dm.conn)
-    dm2 = nn.DeviceMesh(dm.etype, dm.n_nodes, d_conn, dm.elem_ptr, dm.elem_type)
-    h_rp = {k: torch.empty(rp.numel(), dtype=torch.int64, pin_memory=True) for k, (rp, _) in out.items()}
-    h_col = {k: torch.empty(col.numel(), dtype=torch.int32, pin_memory=True) for k, (_, col) in out.items()}
-    stream = torch.cuda.current_stream(dev)
-    h2d = d2h = 0
+    slots = []
+    for k in range(2):
+        d_conn = torch.empty_like(dm.conn)
+        o = out if k == 0 else b.alloc_outputs(dm, want)
+        slots.append(dict(
+            d_conn=d_conn, dm=nn.DeviceMesh(dm.etype, dm.n_nodes, d_conn, dm.elem_ptr, dm.elem_type), out=o,
+            h_rp={c: torch.empty(rp.numel(), dtype=torch.int64, pin_memory=True) for c, (rp, _) in o.items()},
+            h_col={c: torch.empty(col.numel(), dtype=torch.int32, pin_memory=True) for c, (_, col) in o.items()},
+            up=torch.cuda.Event(), built=torch.cuda.Event(), rp=torch.cuda.Event(), done=torch.cuda.Event()))
+        slots[-1]["done"].record(sA)
+    counts = {"h2d": 0, "d2h": 0}
 
-    def one():
-        nonlocal h2d, d2h
-        d_conn.copy_(h_conn, non_blocking=True)
-        st = b.launch(dm2, want, out, ws=ws, ws_bytes=ws_bytes)
+    def start(i):                                  # upload, build and row-pointer download of step i
+        sl = slots[i % 2]
+        sU.wait_event(sl["built"])                 # the build two steps back has read this connectivity
+        with torch.cuda.stream(sU):
+            sl["d_conn"].copy_(h_conn, non_blocking=True)
+        sl["up"].record(sU)
+        sA.wait_event(sl["up"])
+        sA.wait_event(sl["done"])                  # the downloads two steps back have read these outputs
+        st = b.launch(sl["dm"], want, sl["out"], ws=ws, ws_bytes=ws_bytes, stream=sA)
         if st:
             raise nn.NNError(st, "launch")
-        for k, (rp, _) in out.items():
-            h_rp[k].copy_(rp, non_blocking=True)
-        stream.synchronize()
-        for k, (_, col) in out.items():
-            n = int(h_rp[k][-1])
-            h_col[k][:n].copy_(col[:n], non_blocking=True)
-            d2h += 8 * h_rp[k].numel() + 4 * n
-        stream.synchronize()
-        h2d += h_conn.numel() * 4
+        sl["built"].record(sA)
+        sD.wait_event(sl["built"])
+        with torch.cuda.stream(sD):
+            for c, (rp, _) in sl["out"].items():
+                sl["h_rp"][c].copy_(rp, non_blocking=True)
+        sl["rp"].record(sD)
+        counts["h2d"] += h_conn.numel() * 4
 
-    one()
-    h2d = d2h = 0
+    def finish(i):                                 # column downloads of step i, sized by its row pointers
+        sl = slots[i % 2]
+        sl["rp"].synchronize()
+        with torch.cuda.stream(sD):
+            for c, (_, col) in sl["out"].items():
+                n = int(sl["h_rp"][c][-1])
+                sl["h_col"][c][:n].copy_(col[:n], non_blocking=True)
+                counts["d2h"] += 8 * sl["h_rp"][c].numel() + 4 * n
+        sl["done"].record(sD)
+
+    start(0)
+    finish(0)
     torch.cuda.synchronize(dev)
+    counts["h2d"] = counts["d2h"] = 0
     t0 = time.perf_counter()
-    for _ in range(steps):
-        one()
+    for i in range(steps):
+        start(i)
+        if i > 0:
+            finish(i - 1)
+    finish(steps - 1)
+    torch.cuda.synchronize(dev)
     dt = time.perf_counter() - t0
     if int(b.status.item()) != 0:
         raise RuntimeError("device status after end-to-end leg: " + nn.STATUS[int(b.status.item())])
     return {"value": world * mesh.n_elems * steps / dt / 1e6, "unit": "Melem/s",
-            "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
-            "ms_per_step": dt * 1e3 / steps}
+            "h2d_bytes_per_step": counts["h2d"] // steps, "d2h_bytes_per_step": counts["d2h"] // steps,
+            "ms_per_step": dt * 1e3 / steps, "pipelined": "uploads, builds and downloads on three streams"}
 
 
 def time_adjacency(torch, nn, b, dm, out, flush, stream, steps):
