@@ -98,6 +98,14 @@ typedef struct nn_handle nn_handle;
 nn_status nn_create(nn_handle** h);
 void nn_destroy(nn_handle* h);
 
+/* A handle for sizing and planning only, on a host with or without a GPU:
+ * nn_query, nn_plan_info, nn_chunk_plan, nn_batch_query and
+ * nn_element_neighbors_query size for a device with `sms` SMs, `smem_optin`
+ * bytes of opt-in shared memory per block and `smem_per_sm` per SM (a GB300:
+ * 152, 232448, 233472).  Compute calls return NN_ERR_ARG on it.  Host
+ * allocation only; free with nn_destroy. */
+nn_status nn_create_offline(nn_handle** h, int32_t sms, int32_t smem_optin, int32_t smem_per_sm);
+
 /* Host-only sizing for a mesh (no device access).  want = NN_WANT_*.
  * *ws_bytes: workspace that a compute call needs (the minimum plus a spill
  * area sized for meshes of ordinary valence; meshes with a few nodes of very
@@ -160,6 +168,60 @@ nn_status nn_neighbor_elements(nn_handle* h, const nn_mesh* mesh, nn_csr* out, v
 nn_status nn_neighbors_both(nn_handle* h, const nn_mesh* mesh, nn_csr* nodes, nn_csr* elems,
                             void* ws, size_t ws_bytes, int32_t* d_status, nn_stream_t stream);
 
+/* ------------------------------------------------------- chunked builds
+ * The same results as nn_neighbor_nodes / nn_neighbor_elements /
+ * nn_neighbors_both (want = NN_WANT_*) with a workspace of the caller's
+ * chosen size, for meshes whose whole-mesh workspace would not fit.  The
+ * paper names its extra device memory as the method's shortcoming and its
+ * future work (Sec. 3.2.2, Sec. 4).  The nodes are cut into chunks of
+ * consecutive ids; each chunk is built in turn, walking all elements but
+ * keeping only its own nodes' incidences, into its rows of the caller's
+ * CSRs.  Peak workspace follows the largest chunk, not the mesh.
+ *
+ * Three steps:
+ *  1. nn_chunk_count (device, asynchronous): incidences per node slab.  A
+ *     slab is 2^shift consecutive node ids; nn_chunk_slabs gives shift and
+ *     the slab count (<= NN_CHUNK_SLABS_MAX).  d_counts: device uint32
+ *     [n_slabs], overwritten.  d_status: set to 0, then any node-range or
+ *     elem_ptr error.
+ *  2. nn_chunk_plan (host only): group consecutive slabs into chunks whose
+ *     workspace, including the spill area nn_query would add, fits ws_bytes.
+ *     counts: the slab counts, copied to the host.  Fills chunks[0 ..
+ *     max_chunks) and *n_chunks.  *ws_needed (may be NULL) is the smallest
+ *     workspace that admits a plan (the largest single slab).  Errors:
+ *     NN_ERR_WORKSPACE when ws_bytes is below that; NN_ERR_CAPACITY when
+ *     more than max_chunks chunks are needed (*n_chunks says how many);
+ *     NN_ERR_ARG when the counts sum above n_conn.
+ *  3. nn_neighbors_chunked (device, asynchronous): build the chunks in
+ *     order on `stream`.  The chunks must tile [0, n_nodes) in order; their
+ *     boundaries need not fall on slabs (nn_chunk_query sizes any chunk).
+ *     Each one's records must be the incidence count of its nodes.
+ *     Wrong counts give NN_ERR_WORKSPACE on the device, not a bad write.
+ *     ws: device memory, 256-byte aligned, at least the plan's ws_bytes.
+ *     Its first 256 bytes hold the running CSR offsets between chunks.
+ * The mesh and output pointers may also be host memory the GPU can address:
+ * pinned (cudaHostAlloc / cudaHostRegister), or pageable on a system that
+ * reports pageable memory access.  That is an out-of-core build, with only
+ * the workspace in device memory.  ws and d_status must be device memory.
+ * The chunks' results equal the single build's bit for bit. */
+#define NN_CHUNK_SLABS_MAX 4096
+typedef struct {
+    int64_t node_lo, node_hi;  /* nodes [node_lo, node_hi) */
+    int64_t records;           /* incidences of those nodes (sum of their slabs' counts) */
+} nn_chunk;
+nn_status nn_chunk_slabs(const nn_mesh* mesh, int* shift, int* n_slabs);
+nn_status nn_chunk_count(nn_handle* h, const nn_mesh* mesh, uint32_t* d_counts, int32_t* d_status,
+                         nn_stream_t stream);
+nn_status nn_chunk_plan(nn_handle* h, const nn_mesh* mesh, int want, const uint32_t* counts, size_t ws_bytes,
+                        nn_chunk* chunks, int max_chunks, int* n_chunks, size_t* ws_needed);
+/* Host only: the workspace one chunk needs in nn_neighbors_chunked.  That is
+ * 256 bytes of running offsets plus what nn_query would give for the chunk's
+ * nodes and records.  For callers that choose their own node ranges. */
+nn_status nn_chunk_query(nn_handle* h, const nn_mesh* mesh, int want, const nn_chunk* chunk, size_t* ws_bytes);
+nn_status nn_neighbors_chunked(nn_handle* h, const nn_mesh* mesh, int want, const nn_chunk* chunks, int n_chunks,
+                               nn_csr* nodes, nn_csr* elems, void* ws, size_t ws_bytes, int32_t* d_status,
+                               nn_stream_t stream);
+
 /* ------------------------------------------------------------- batches
  * Many meshes of any types, each with its own outputs, built by ONE launch
  * sequence (batch init, histogram, offsets, partition, bucket pass) over the
@@ -211,12 +273,12 @@ nn_status nn_generate_grid(int32_t type, int64_t n, uint64_t seed, int permute_n
 /* Per-stage device timing (used by the benchmark).  While enabled, compute
  * calls record CUDA events on their stream between their stages:
  *   0 workspace/status init, 1 bucket histogram, 2 bucket offsets,
- *   3 partition (record write), 4 bucket build (rows + CSR write).
+ *   3 partition (record write), 4 bucket pass (element CSR, node rows to
+ *   scratch), 5 node-row placement.
  * nn_profile_read waits for the recorded events and returns, per stage, the
  * summed milliseconds over the calls since profiling was enabled, and the
  * number of calls.  n_stages <= NN_PROFILE_STAGES.  Enabling twice resets the
- * sums.  Stages: status and workspace init, histogram, offsets, partition,
- * bucket pass, node-row placement. */
+ * sums.  Chunked builds and batches record no stages. */
 #define NN_PROFILE_STAGES 6
 nn_status nn_profile_enable(nn_handle* h, int enable);
 nn_status nn_profile_read(nn_handle* h, double* ms, int64_t* calls, int n_stages);

@@ -15,6 +15,7 @@ cudaError_t set_bucket_smem_all(size_t bytes);
 
 struct nn_handle {
     int device = 0;
+    bool offline = false;      // nn_create_offline: sizing and planning only, no compute calls
     int sms = 0;
     size_t smem_optin = 0;     // max dynamic shared memory per block
     size_t bucket_smem = 0;    // largest dynamic shared memory of the bucket kernel
@@ -48,7 +49,9 @@ int npe_host(int t) { return t == NN_TRI ? 3 : (t == NN_HEX ? 8 : 4); }
 
 struct Plan {
     int type = 0, want = 0, k = 0;
-    int64_t N = 0, T = 0, n_conn = 0;
+    // N: nodes of this build's range (first node `lo`); n_conn: its records
+    // (incidences of those nodes); a whole mesh has lo = 0 and both totals
+    int64_t N = 0, T = 0, n_conn = 0, lo = 0;
     RecFmt fmt{};
     int64_t B = 0;
     int64_t hist_chunk = 1;
@@ -81,16 +84,23 @@ nn_status check_mesh(const nn_mesh* m) {
     return NN_OK;
 }
 
-nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
+// Plan of a build over the nodes [lo, lo + span) of mesh m, which have
+// `records` incidences: the element walk covers the whole mesh, the record
+// arrays and node tables only this range.  Record fields stay sized by the
+// whole mesh (node and element ids are global).
+nn_status make_plan_range(const nn_handle* h, const nn_mesh* m, int want, int64_t lo, int64_t span, int64_t records,
+                          Plan* P) {
     nn_status st = check_mesh(m);
     if (st != NN_OK) return st;
     if (want < 1 || want > 3) return NN_ERR_ARG;
+    if (lo < 0 || span < 0 || lo + span > m->n_nodes || records < 0 || records > m->n_conn) return NN_ERR_ARG;
     Plan p;
     p.type = m->type;
     p.want = want;
-    p.N = m->n_nodes;
+    p.N = span;
+    p.lo = lo;
     p.T = m->n_elems;
-    p.n_conn = m->n_conn;
+    p.n_conn = records;
     p.k = (m->type == NN_TRI || m->type == NN_QUAD) ? 2 : 3;
 
     // bucket kernel shape.  Every node goes to one lane, which holds up to
@@ -140,7 +150,7 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     f.want = want;
     f.k = p.k;
     f.eb = bits_for(p.T > 0 ? (uint64_t)(p.T - 1) : 0);
-    f.nb = bits_for((uint64_t)p.N);
+    f.nb = bits_for((uint64_t)m->n_nodes);
     f.off_nf = sb;
     f.off_e = sb + 1;
     f.off_n = (want & NN_WANT_ELEMS) ? sb + 1 + f.eb : sb;
@@ -173,7 +183,8 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
 
     p.area_words = (uint32_t)((p.bucket_smem - fixed_of(sb)) / 4);
     int per_sm = 1;
-    if (bucket_occupancy(&per_sm, p.bucket_threads, p.wide, p.bucket_smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+    if (h->offline || bucket_occupancy(&per_sm, p.bucket_threads, p.wide, p.bucket_smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
     p.bucket_grid = (int)std::min<int64_t>(p.B, (int64_t)h->sms * per_sm);
 
     // workspace layout
@@ -212,6 +223,12 @@ nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
     return NN_OK;
 }
 
+nn_status make_plan(const nn_handle* h, const nn_mesh* m, int want, Plan* P) {
+    nn_status st = check_mesh(m);
+    if (st != NN_OK) return st;
+    return make_plan_range(h, m, want, 0, m->n_nodes, m->n_conn, P);
+}
+
 void prof_flush(nn_handle* h) {
     if (!h->pending) return;
     h->pending = false;
@@ -227,18 +244,28 @@ void prof_mark(nn_handle* h, int i, cudaStream_t s) {
     if (h->prof) cudaEventRecord(h->ev[i], s);
 }
 
-nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* elems, void* ws,
-              size_t ws_bytes, int32_t* d_status, cudaStream_t s) {
-    if (!h || !d_status) return NN_ERR_ARG;
-    Plan p;
-    nn_status st = make_plan(h, m, want, &p);
-    if (st != NN_OK) return st;
+nn_status enqueue(nn_handle* h, const nn_mesh* m, const Plan& p, nn_csr* nodes, nn_csr* elems, uint8_t* w,
+                  size_t ws_bytes, const int64_t* base, int32_t* d_status, bool prof, cudaStream_t s);
+
+// Argument checks shared by the single and chunked builds.
+nn_status check_outputs(int want, const nn_csr* nodes, const nn_csr* elems) {
     if ((want & NN_WANT_NODES) && (!nodes || !nodes->row_ptr || nodes->col_capacity < 0 ||
                                    (nodes->col_capacity > 0 && !nodes->col)))
         return NN_ERR_ARG;
     if ((want & NN_WANT_ELEMS) && (!elems || !elems->row_ptr || elems->col_capacity < 0 ||
                                    (elems->col_capacity > 0 && !elems->col)))
         return NN_ERR_ARG;
+    return NN_OK;
+}
+
+nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* elems, void* ws,
+              size_t ws_bytes, int32_t* d_status, cudaStream_t s) {
+    if (!h || h->offline || !d_status) return NN_ERR_ARG;
+    Plan p;
+    nn_status st = make_plan(h, m, want, &p);
+    if (st != NN_OK) return st;
+    st = check_outputs(want, nodes, elems);
+    if (st != NN_OK) return st;
     if (ws_bytes < p.ws_min || (!ws && p.ws_min > 0)) return NN_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(ws) & (ALIGN - 1)) return NN_ERR_ARG;
 
@@ -251,14 +278,30 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
         if ((want & NN_WANT_ELEMS) && cudaMemsetAsync(elems->row_ptr, 0, 8, s) != cudaSuccess) return NN_ERR_CUDA;
         return NN_OK;
     }
+    st = enqueue(h, m, p, nodes, elems, w, ws_bytes, nullptr, d_status, h->prof, s);
+    if (st == NN_OK && h->prof) h->pending = true;
+    return st;
+}
+
+// Enqueue the kernels of plan p: rows p.lo .. p.lo + p.N - 1 of the CSRs.
+// base: the running {element, node} CSR bases of a chunked build on the
+// device, added to every row pointer and col position (nullptr: 0).
+nn_status enqueue(nn_handle* h, const nn_mesh* m, const Plan& p, nn_csr* nodes, nn_csr* elems, uint8_t* w,
+                  size_t ws_bytes, const int64_t* base, int32_t* d_status, bool prof, cudaStream_t s) {
+    const int want = p.want;
+    auto mark = [&](int i) {
+        if (prof) prof_mark(h, i, s);
+    };
     if (cudaMemsetAsync(w + p.zero_begin, 0, p.zero_end - p.zero_begin, s) != cudaSuccess) return NN_ERR_CUDA;
 
     uint32_t* ctrl = reinterpret_cast<uint32_t*>(w + p.off_ctrl);
     EmitParams ep{};
     ep.type = p.type;
-    ep.n_nodes = p.N;
+    ep.n_nodes = m->n_nodes;
     ep.n_elems = p.T;
-    ep.n_conn = p.n_conn;
+    ep.n_conn = m->n_conn;
+    ep.node_lo = p.lo;
+    ep.node_span = p.N;
     ep.conn = m->conn;
     ep.elem_ptr = m->elem_ptr;
     ep.elem_type = m->elem_type;
@@ -304,15 +347,16 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
     const size_t spill_bytes = ws_bytes > p.off_spill ? ws_bytes - p.off_spill : 0;
     bp.spill_words = spill_bytes / 4;
     if (want & NN_WANT_NODES) {
-        bp.rp_n = nodes->row_ptr;
+        bp.rp_n = nodes->row_ptr + p.lo;
         bp.col_n = nodes->col;
         bp.cap_n = nodes->col_capacity;
     }
     if (want & NN_WANT_ELEMS) {
-        bp.rp_e = elems->row_ptr;
+        bp.rp_e = elems->row_ptr + p.lo;
         bp.col_e = elems->col;
         bp.cap_e = elems->col_capacity;
     }
+    bp.base = base;
     bp.status = d_status;
     bp.area_words = p.area_words;
     bp.wide = p.wide;
@@ -320,20 +364,20 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
     bp.ubk = reinterpret_cast<uint32_t*>(w + p.off_ubk);
     bp.nloc = reinterpret_cast<uint32_t*>(w + p.off_nloc);
 
-    prof_mark(h, 1, s);
+    mark(1);
     if (launch_hist(ep, p.emit_smem, s) != cudaSuccess) return NN_ERR_CUDA;
-    prof_mark(h, 2, s);
+    mark(2);
     if (launch_offsets(op, s) != cudaSuccess) return NN_ERR_CUDA;
-    prof_mark(h, 3, s);
+    mark(3);
     if (p.fmt.cshift >= 0) {
         if (launch_part_sorted(ep, op.bstart, p.G_fine, s) != cudaSuccess) return NN_ERR_CUDA;
     } else if (launch_part(ep, s) != cudaSuccess) {
         return NN_ERR_CUDA;
     }
-    prof_mark(h, 4, s);
+    mark(4);
     if (launch_bucket(bp, p.bucket_grid, p.bucket_threads, p.bucket_smem, s) != cudaSuccess)
         return NN_ERR_CUDA;
-    prof_mark(h, 5, s);
+    mark(5);
     if (want & NN_WANT_NODES) {
         CompactParams cp{};
         cp.n_buckets = p.B;
@@ -341,6 +385,7 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
         cp.sb = p.fmt.sb;
         cp.k = p.k;
         cp.n_nodes = p.N;
+        cp.base = base;
         cp.bstart = bp.bstart;
         cp.ubk = bp.ubk;
         cp.nloc = bp.nloc;
@@ -348,15 +393,14 @@ nn_status run(nn_handle* h, const nn_mesh* m, int want, nn_csr* nodes, nn_csr* e
         cp.nstart = reinterpret_cast<uint64_t*>(w + p.off_nstart);
         cp.lb_state = reinterpret_cast<uint64_t*>(w + p.off_lb_ns);
         cp.ticket = ctrl + 4;
-        cp.rp_n = nodes->row_ptr;
+        cp.rp_n = nodes->row_ptr + p.lo;
         cp.col_n = nodes->col;
         cp.cap_n = nodes->col_capacity;
         cp.status = d_status;
         if (launch_node_compact(cp, (int)std::min<int64_t>(p.B, (int64_t)h->sms * 8), s) != cudaSuccess)
             return NN_ERR_CUDA;
     }
-    prof_mark(h, 6, s);
-    if (h->prof) h->pending = true;
+    mark(6);
     return NN_OK;
 }
 
@@ -498,6 +542,7 @@ nn_status batch_prepare(nn_handle* h, const nn_batch_caps* c, const nn_mesh* mes
 
 nn_status batch_launch(nn_handle* h, const nn_batch_caps* c, const void* staging, void* ws, size_t ws_bytes,
                        cudaStream_t s) {
+    if (!h || h->offline) return NN_ERR_ARG;
     BatchPlan bp;
     nn_status st = batch_plan(h, c, &bp);
     if (st != NN_OK) return st;
@@ -630,6 +675,20 @@ nn_status nn_create(nn_handle** out) {
     return NN_OK;
 }
 
+nn_status nn_create_offline(nn_handle** out, int32_t sms, int32_t smem_optin, int32_t smem_per_sm) {
+    if (!out || sms < 1 || smem_optin < 64 * 1024 || smem_per_sm < smem_optin) return NN_ERR_ARG;
+    nn_handle* h = new (std::nothrow) nn_handle();
+    if (!h) return NN_ERR_ARG;
+    h->device = -1;
+    h->offline = true;
+    h->sms = sms;
+    h->smem_optin = (size_t)smem_optin;
+    h->smem_per_sm = (size_t)smem_per_sm;
+    h->bucket_smem = h->smem_optin - 1024;
+    *out = h;
+    return NN_OK;
+}
+
 void nn_destroy(nn_handle* h) {
     if (!h) return;
     for (cudaEvent_t e : h->ev)
@@ -638,7 +697,7 @@ void nn_destroy(nn_handle* h) {
 }
 
 nn_status nn_profile_enable(nn_handle* h, int enable) {
-    if (!h) return NN_ERR_ARG;
+    if (!h || h->offline) return NN_ERR_ARG;
     if (enable && !h->ev[0])
         for (cudaEvent_t& e : h->ev)
             if (cudaEventCreate(&e) != cudaSuccess) return NN_ERR_CUDA;
@@ -694,7 +753,7 @@ nn_status nn_element_neighbors_query(nn_handle* h, const nn_mesh* mesh, size_t* 
 
 nn_status nn_element_neighbors(nn_handle* h, const nn_mesh* mesh, const nn_csr* node_elems, nn_csr* out, void* ws,
                                size_t ws_bytes, int32_t* d_status, nn_stream_t stream) {
-    if (!h || !node_elems || !node_elems->row_ptr || !out || !out->row_ptr || !d_status) return NN_ERR_ARG;
+    if (!h || h->offline || !node_elems || !node_elems->row_ptr || !out || !out->row_ptr || !d_status) return NN_ERR_ARG;
     nn_status st = check_mesh(mesh);
     if (st != NN_OK) return st;
     if (out->col_capacity < 0 || (out->col_capacity > 0 && !out->col)) return NN_ERR_ARG;
@@ -757,6 +816,189 @@ nn_status nn_neighbor_elements(nn_handle* h, const nn_mesh* mesh, nn_csr* out, v
 nn_status nn_neighbors_both(nn_handle* h, const nn_mesh* mesh, nn_csr* nodes, nn_csr* elems, void* ws,
                             size_t ws_bytes, int32_t* d_status, nn_stream_t stream) {
     return run(h, mesh, NN_WANT_BOTH, nodes, elems, ws, ws_bytes, d_status, reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ------------------------------------------------------ chunked builds
+
+namespace {
+
+// Whether kernels on device `dev` may dereference ptr: device or managed
+// memory, pinned host memory mapped at the same address (unified
+// addressing), or any host memory where the device reads pageable memory.
+bool addressable(const void* ptr, int dev) {
+    if (!ptr) return true;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return true;
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer == ptr;
+    int pageable = 0;
+    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) return false;
+    return pageable != 0;
+}
+
+bool on_device(const void* ptr) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool mesh_addressable(const nn_mesh* m, int dev) {
+    return addressable(m->conn, dev) && addressable(m->elem_ptr, dev) && addressable(m->elem_type, dev);
+}
+
+}  // namespace
+
+nn_status nn_chunk_slabs(const nn_mesh* mesh, int* shift, int* n_slabs) {
+    nn_status st = check_mesh(mesh);
+    if (st != NN_OK) return st;
+    int sh = 0;
+    while (((mesh->n_nodes + (1ll << sh) - 1) >> sh) > NN_CHUNK_SLABS_MAX) ++sh;
+    if (shift) *shift = sh;
+    if (n_slabs) *n_slabs = (int)((mesh->n_nodes + (1ll << sh) - 1) >> sh);
+    return NN_OK;
+}
+
+nn_status nn_chunk_count(nn_handle* h, const nn_mesh* mesh, uint32_t* d_counts, int32_t* d_status,
+                         nn_stream_t stream) {
+    if (!h || h->offline || !d_status) return NN_ERR_ARG;
+    int shift = 0, ns = 0;
+    nn_status st = nn_chunk_slabs(mesh, &shift, &ns);
+    if (st != NN_OK) return st;
+    if (ns > 0 && !d_counts) return NN_ERR_ARG;
+    if (!on_device(d_status) || (ns > 0 && !on_device(d_counts)) || !mesh_addressable(mesh, h->device))
+        return NN_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return NN_ERR_CUDA;
+    if (ns == 0) return NN_OK;
+    if (cudaMemsetAsync(d_counts, 0, (size_t)ns * 4, s) != cudaSuccess) return NN_ERR_CUDA;
+    if (mesh->n_elems == 0) return NN_OK;
+    EmitParams ep{};
+    ep.type = mesh->type;
+    ep.n_nodes = mesh->n_nodes;
+    ep.n_elems = mesh->n_elems;
+    ep.n_conn = mesh->n_conn;
+    ep.conn = mesh->conn;
+    ep.elem_ptr = mesh->elem_ptr;
+    ep.elem_type = mesh->elem_type;
+    // element-walk CTAs as in a build: two per SM, each a fixed slice of elements
+    const int64_t n_units = (mesh->n_elems + (mesh->type == NN_TRI ? 3 : 0)) / (mesh->type == NN_TRI ? 4 : 1);
+    ep.n_cta = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sms * 2, (n_units + 2047) / 2048));
+    ep.status = d_status;
+    return launch_slab_count(ep, shift, ns, d_counts, s) == cudaSuccess ? NN_OK : NN_ERR_CUDA;
+}
+
+nn_status nn_chunk_query(nn_handle* h, const nn_mesh* mesh, int want, const nn_chunk* chunk, size_t* ws_bytes) {
+    if (!h || !chunk || chunk->node_hi <= chunk->node_lo) return NN_ERR_ARG;
+    Plan p;
+    nn_status st = make_plan_range(h, mesh, want, chunk->node_lo, chunk->node_hi - chunk->node_lo, chunk->records, &p);
+    if (st != NN_OK) return st;
+    if (ws_bytes) *ws_bytes = ALIGN + p.ws_rec;  // the running CSR bases, then the chunk's plan
+    return NN_OK;
+}
+
+nn_status nn_chunk_plan(nn_handle* h, const nn_mesh* mesh, int want, const uint32_t* counts, size_t ws_bytes,
+                        nn_chunk* chunks, int max_chunks, int* n_chunks, size_t* ws_needed) {
+    if (!h || !n_chunks || max_chunks < 0 || (max_chunks > 0 && !chunks)) return NN_ERR_ARG;
+    int shift = 0, ns = 0;
+    nn_status st = nn_chunk_slabs(mesh, &shift, &ns);
+    if (st != NN_OK) return st;
+    if (want < 1 || want > 3 || (ns > 0 && !counts)) return NN_ERR_ARG;
+    const int64_t N = mesh->n_nodes;
+    int64_t total = 0;
+    for (int i = 0; i < ns; ++i) total += counts[i];
+    if (total > mesh->n_conn) return NN_ERR_ARG;  // not this mesh's counts
+    // workspace of the chunk of slabs i..j
+    auto need = [&](int i, int j, int64_t rec, size_t* out) {
+        const nn_chunk k{(int64_t)i << shift, std::min<int64_t>(N, (int64_t)(j + 1) << shift), rec};
+        return nn_chunk_query(h, mesh, want, &k, out);
+    };
+    // the smallest workspace that admits a plan: the largest single slab
+    size_t worst = ALIGN;
+    for (int i = 0; i < ns; ++i) {
+        size_t w1 = 0;
+        if ((st = need(i, i, counts[i], &w1)) != NN_OK) return st;
+        worst = std::max(worst, w1);
+    }
+    if (ws_needed) *ws_needed = worst;
+    if (worst > ws_bytes) {
+        *n_chunks = 0;
+        return NN_ERR_WORKSPACE;
+    }
+    // greedy: each chunk takes slabs while its plan still fits the workspace
+    int n = 0;
+    for (int i = 0; i < ns;) {
+        int j = i;
+        int64_t rec = counts[i];
+        while (j + 1 < ns) {
+            size_t w2 = 0;
+            if (need(i, j + 1, rec + counts[j + 1], &w2) != NN_OK || w2 > ws_bytes) break;
+            ++j;
+            rec += counts[j];
+        }
+        if (n < max_chunks)
+            chunks[n] = nn_chunk{(int64_t)i << shift, std::min<int64_t>(N, (int64_t)(j + 1) << shift), rec};
+        ++n;
+        i = j + 1;
+    }
+    *n_chunks = n;
+    return n > max_chunks ? NN_ERR_CAPACITY : NN_OK;
+}
+
+nn_status nn_neighbors_chunked(nn_handle* h, const nn_mesh* mesh, int want, const nn_chunk* chunks, int n_chunks,
+                               nn_csr* nodes, nn_csr* elems, void* ws, size_t ws_bytes, int32_t* d_status,
+                               nn_stream_t stream) {
+    if (!h || h->offline || !d_status || n_chunks < 0 || (n_chunks > 0 && !chunks)) return NN_ERR_ARG;
+    nn_status st = check_mesh(mesh);
+    if (st != NN_OK) return st;
+    if (want < 1 || want > 3) return NN_ERR_ARG;
+    st = check_outputs(want, nodes, elems);
+    if (st != NN_OK) return st;
+    if (!ws) return NN_ERR_WORKSPACE;
+    if ((reinterpret_cast<uintptr_t>(ws) & (ALIGN - 1)) || !on_device(ws) || !on_device(d_status) || !mesh_addressable(mesh, h->device)) return NN_ERR_ARG;
+    if ((want & NN_WANT_NODES) && (!addressable(nodes->row_ptr, h->device) || !addressable(nodes->col, h->device)))
+        return NN_ERR_ARG;
+    if ((want & NN_WANT_ELEMS) && (!addressable(elems->row_ptr, h->device) || !addressable(elems->col, h->device)))
+        return NN_ERR_ARG;
+    const int64_t N = mesh->n_nodes;
+    // the chunks must tile [0, N) in order
+    if (N > 0 && (n_chunks == 0 || chunks[0].node_lo != 0 || chunks[n_chunks - 1].node_hi != N)) return NN_ERR_ARG;
+    for (int c = 0; c < n_chunks; ++c) {
+        const nn_chunk& k = chunks[c];
+        if (k.node_hi <= k.node_lo || (c > 0 && k.node_lo != chunks[c - 1].node_hi) || k.records < 0 ||
+            k.records > mesh->n_conn)
+            return NN_ERR_ARG;
+        Plan p;
+        if ((st = make_plan_range(h, mesh, want, k.node_lo, k.node_hi - k.node_lo, k.records, &p)) != NN_OK)
+            return st;
+        if (ALIGN + p.ws_min > ws_bytes) return NN_ERR_WORKSPACE;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t* w = static_cast<uint8_t*>(ws);
+    int64_t* base = reinterpret_cast<int64_t*>(w);
+    if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return NN_ERR_CUDA;
+    if (cudaMemsetAsync(base, 0, 2 * sizeof(int64_t), s) != cudaSuccess) return NN_ERR_CUDA;
+    if (N == 0) {
+        if ((want & NN_WANT_NODES) && cudaMemsetAsync(nodes->row_ptr, 0, 8, s) != cudaSuccess) return NN_ERR_CUDA;
+        if ((want & NN_WANT_ELEMS) && cudaMemsetAsync(elems->row_ptr, 0, 8, s) != cudaSuccess) return NN_ERR_CUDA;
+        return NN_OK;
+    }
+    uint8_t* cw = w + ALIGN;
+    for (int c = 0; c < n_chunks; ++c) {
+        Plan p;
+        make_plan_range(h, mesh, want, chunks[c].node_lo, chunks[c].node_hi - chunks[c].node_lo, chunks[c].records, &p);
+        if ((st = enqueue(h, mesh, p, nodes, elems, cw, ws_bytes - ALIGN, base, d_status, false, s)) != NN_OK)
+            return st;
+        const uint32_t* estart = (want & NN_WANT_ELEMS) ? reinterpret_cast<const uint32_t*>(cw + p.off_estart) : nullptr;
+        const uint64_t* nstart = (want & NN_WANT_NODES) ? reinterpret_cast<const uint64_t*>(cw + p.off_nstart) : nullptr;
+        if (launch_chunk_advance(base, estart, nstart, p.B, s) != cudaSuccess) return NN_ERR_CUDA;
+    }
+    return NN_OK;
 }
 
 nn_status nn_batch_query(nn_handle* h, const nn_batch_caps* caps, size_t* ws_bytes, size_t* staging_bytes) {

@@ -297,9 +297,10 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_bucket(BucketParams 
         const uint64_t ucap = insm ? (uint64_t)p.area_words - R - Eb : (uint64_t)p.area_words;
 
         // the element rows' offset: a prefix of the record counts, known
-        // before this pass (for a batch, relative to the mesh's first bucket)
+        // before this pass (for a batch, relative to the mesh's first bucket;
+        // for a chunk, after the earlier chunks' entries)
         if (want_e && tid == 0) {
-            const uint64_t ge = (uint64_t)(p.estart[b] - p.estart[first]);
+            const uint64_t ge = (uint64_t)(p.estart[b] - p.estart[first]) + (p.base ? (uint64_t)p.base[0] : 0ull);
             misc[1] = ge;
             if (ge + Eb > (uint64_t)sh_out.cap_e) set_status(status, NN_ERR_CAPACITY);
         }

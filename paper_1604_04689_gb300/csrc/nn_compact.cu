@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(COPY_THREADS) k_node_copy(CompactParams p) {
             cap = M.cap_n;
             status = M.status;
         }
-        const uint64_t gn = p.nstart[b] - p.nstart[first];
+        const uint64_t gn = p.nstart[b] - p.nstart[first] + (p.base ? (uint64_t)p.base[1] : 0ull);
         const uint32_t ub = p.ubk[b];
         const int64_t v0 = (b - first) << sb;
         const int nb = (int)(N - v0 < ((int64_t)1 << sb) ? N - v0 : ((int64_t)1 << sb));
@@ -83,7 +83,22 @@ __global__ void __launch_bounds__(COPY_THREADS) k_node_copy(CompactParams p) {
     }
 }
 
+// Chunked builds run one node range after another into the same CSRs; after
+// a chunk, the running bases move past its element and node entries.
+__global__ void k_chunk_advance(int64_t* base, const uint32_t* estart, const uint64_t* nstart, int64_t B) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (estart) base[0] += (int64_t)estart[B];
+        if (nstart) base[1] += (int64_t)nstart[B];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_chunk_advance(int64_t* base, const uint32_t* estart, const uint64_t* nstart, int64_t B,
+                                 cudaStream_t s) {
+    k_chunk_advance<<<1, 32, 0, s>>>(base, estart, nstart, B);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_node_compact(const CompactParams& p, int copy_grid, cudaStream_t s) {
     const int64_t B = p.n_buckets_cap;

@@ -16,6 +16,23 @@ namespace nn {
 
 namespace {
 
+// A checked node id relative to the build's first node (vr), and whether it
+// lies in the build's node range.  RANGED = false is a whole-mesh build:
+// every checked id is in range and vr = v, with no arithmetic at all.
+template <bool RANGED>
+__device__ __forceinline__ bool node_in(const EmitParams& p, int32_t v, uint32_t& vr) {
+    if constexpr (RANGED) {
+        const uint64_t r = (uint64_t)((int64_t)v - p.node_lo);  // a node before the range wraps above every span
+        vr = (uint32_t)r;
+        return r < (uint64_t)p.node_span;
+    } else {
+        vr = (uint32_t)v;
+        return true;
+    }
+}
+
+__host__ __device__ inline bool ranged(const EmitParams& p) { return p.node_lo != 0 || p.node_span != p.n_nodes; }
+
 // Per-incidence callback signature: (v, nf, e, x0, x1, x2) with x_s = -1 for none.
 template <int TYPE, class F>
 __device__ __forceinline__ void visit_elem(const int32_t* nd, int64_t e, int64_t n_nodes, int32_t* status,
@@ -103,7 +120,7 @@ __device__ __forceinline__ void walk_cta(const EmitParams& p, F&& f) {
 // Counts per bucket of this CTA's element slice, in shared memory.  When the
 // buckets outnumber the shared counters (hist_chunk), the slice is walked once
 // per chunk of buckets.
-template <int TYPE>
+template <int TYPE, bool RANGED>
 __global__ void __launch_bounds__(EMIT_THREADS) k_hist(EmitParams p) {
     extern __shared__ uint32_t sh_hist[];
     const int64_t B = p.n_buckets;
@@ -114,14 +131,32 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_hist(EmitParams p) {
         for (int64_t b = threadIdx.x; b < nc; b += blockDim.x) sh_hist[b] = 0;
         __syncthreads();
         walk_cta<TYPE>(p, [&](int32_t v, int nf, int64_t, int32_t, int32_t, int32_t) {
-            const int64_t b = (int64_t)(v >> sb) - c0;
+            uint32_t vr;
+            if (!node_in<RANGED>(p, v, vr)) return;  // another chunk's node
+            const int64_t b = (int64_t)(vr >> sb) - c0;
             if (b >= 0 && b < nc) atomicAdd(&sh_hist[b], 1u);
-            if (nf && c0 == 0 && p.nfc) atomicAdd(&p.nfc[v >> sb], 1u);  // rare: degenerate elements only
+            if (nf && c0 == 0 && p.nfc) atomicAdd(&p.nfc[vr >> sb], 1u);  // rare: degenerate elements only
         });
         __syncthreads();
         for (int64_t b = threadIdx.x; b < nc; b += blockDim.x) row[c0 + b] = sh_hist[b];
         __syncthreads();
     }
+}
+
+// Incidences per node slab (2^shift consecutive nodes), for planning a
+// chunked build: one shared counter per slab, added to counts at the end.
+template <int TYPE>
+__global__ void __launch_bounds__(EMIT_THREADS) k_slab_count(EmitParams p, int shift, int n_slabs, uint32_t* counts) {
+    __shared__ uint32_t sh_cnt[NN_CHUNK_SLABS_MAX];
+    for (int i = threadIdx.x; i < n_slabs; i += blockDim.x) sh_cnt[i] = 0;
+    __syncthreads();
+    walk_cta<TYPE>(p, [&](int32_t v, int, int64_t, int32_t, int32_t, int32_t) {
+        const int s = v >> shift;  // v is a checked node id, so s < n_slabs
+        if (s < n_slabs) atomicAdd(&sh_cnt[s], 1u);
+    });
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_slabs; i += blockDim.x)
+        if (sh_cnt[i]) atomicAdd(&counts[i], sh_cnt[i]);
 }
 
 // Load one work unit (4 triangles or one element); returns the runtime type
@@ -196,7 +231,7 @@ struct PartShape {
     static constexpr int UPT = (TYPE == NN_TRI) ? 1 : (NPE == 8 ? 2 : 3);  // units per thread per round
 };
 
-template <int TYPE, int RB>
+template <int TYPE, int RB, bool RANGED>
 __global__ void __launch_bounds__(PART_THREADS, 2) k_part(EmitParams p) {
     using S = PartShape<TYPE>;
     constexpr int UNIT = S::UNIT, NPE = S::NPE, UPT = S::UPT, NI = NPE * UNIT;
@@ -223,7 +258,8 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_part(EmitParams p) {
             for (int j = 0; j < NI; ++j) {
                 const int w = j / NPE, i = j % NPE;
                 pos[k][j] = 0xFFFFFFFFu;
-                if (ok[k][w] && i < npe) pos[k][j] = atomicAdd(&p.gcur[(uint32_t)nd[k][j] >> f.sb], 1u);
+                uint32_t vr;
+                if (ok[k][w] && i < npe && node_in<RANGED>(p, nd[k][j], vr)) pos[k][j] = atomicAdd(&p.gcur[vr >> f.sb], 1u);
             }
         }
 #pragma unroll
@@ -239,7 +275,9 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_part(EmitParams p) {
 #pragma unroll
                 for (int q = 0; q < NPE; ++q) nf |= (q < i) && (e_nd[q] == v);
                 const int K = TYPE == NN_MIXED ? k_of(tk) : ElemT<(TYPE == NN_MIXED ? NN_HEX : TYPE)>::K;
-                Rec r{(uint64_t)((uint32_t)v & vmask), 0};
+                uint32_t vr;
+                node_in<RANGED>(p, v, vr);
+                Rec r{(uint64_t)(vr & vmask), 0};
                 if (f.want & NN_WANT_ELEMS) {
                     rec_put(r, (uint64_t)nf, f.off_nf);
                     rec_put(r, (uint64_t)((ub + k) * UNIT + w), f.off_e);
@@ -320,15 +358,16 @@ constexpr int FINE_DIGITS = 4096;  // buckets per coarse region: at most 256 x 4
 __host__ __device__ constexpr size_t fine_smem(int nd) { return (size_t)FINE_TILE * 18 + 3 * (size_t)nd * 4 + 257 * 4; }
 constexpr size_t FINE_SMEM = fine_smem(FINE_DIGITS);
 
+// vr: the node's id relative to the build's first node
 template <int TYPE>
-__device__ __forceinline__ Rec make_rec(const RecFmt& f, const int32_t* e_nd, int i, int t, int64_t e) {
+__device__ __forceinline__ Rec make_rec(const RecFmt& f, const int32_t* e_nd, int i, int t, int64_t e, uint32_t vr) {
     constexpr int NPE = SortShape<TYPE>::NPE;
     const int32_t v = e_nd[i];
     int nf = 0;
 #pragma unroll
     for (int q = 0; q < NPE; ++q) nf |= (q < i) && (e_nd[q] == v);
     const int K = TYPE == NN_MIXED ? k_of(t) : ElemT<(TYPE == NN_MIXED ? NN_HEX : TYPE)>::K;
-    Rec r{(uint64_t)((uint32_t)v & ((1u << f.sb) - 1)), 0};
+    Rec r{(uint64_t)(vr & ((1u << f.sb) - 1)), 0};
     if (f.want & NN_WANT_ELEMS) {
         rec_put(r, (uint64_t)nf, f.off_nf);
         rec_put(r, (uint64_t)e, f.off_e);
@@ -342,7 +381,7 @@ __device__ __forceinline__ Rec make_rec(const RecFmt& f, const int32_t* e_nd, in
             rec_put(r, y == v ? 0ull : (uint64_t)(uint32_t)(y + 1), f.off_n + s * f.nb);
         }
     }
-    if (f.cshift > 0) rec_put(r, (uint64_t)(((uint32_t)v >> f.sb) & ((1u << f.cshift) - 1)), f.off_fb);
+    if (f.cshift > 0) rec_put(r, (uint64_t)((vr >> f.sb) & ((1u << f.cshift) - 1)), f.off_fb);
     return r;
 }
 
@@ -359,7 +398,7 @@ __device__ __forceinline__ ulonglong2 load_rec2(const uint8_t* base, uint64_t po
 
 // First (or only) pass: records from the connectivity, radix digit = coarse
 // region (two levels) or bucket (one level, at most 256 buckets).
-template <int TYPE, int RB>
+template <int TYPE, int RB, bool RANGED>
 __global__ void __launch_bounds__(SORT_THREADS) k_part_coarse(EmitParams p) {
     using S = SortShape<TYPE>;
     constexpr int UNIT = S::UNIT, NPE = S::NPE, UPT = S::UPT, NI = S::NI, TILE = S::TILE;
@@ -398,8 +437,9 @@ __global__ void __launch_bounds__(SORT_THREADS) k_part_coarse(EmitParams p) {
                 const int w = j / NPE, i = j % NPE;
                 dg[k][j] = 0;
                 rk[k][j] = 0xFFFF;
-                if (ok[k][w] && i < npe) {
-                    const uint32_t d = (uint32_t)nd[k][j] >> dshift;
+                uint32_t vr;
+                if (ok[k][w] && i < npe && node_in<RANGED>(p, nd[k][j], vr)) {
+                    const uint32_t d = vr >> dshift;
                     dg[k][j] = (uint8_t)d;
                     rk[k][j] = (uint16_t)atomicAdd(&hist[d], 1u);
                 }
@@ -415,7 +455,9 @@ __global__ void __launch_bounds__(SORT_THREADS) k_part_coarse(EmitParams p) {
             for (int j = 0; j < NI; ++j) {
                 if (rk[k][j] == 0xFFFF) continue;
                 const int w = j / NPE, i = j % NPE;
-                const Rec r = make_rec<TYPE>(f, nd[k] + w * NPE, i, t[k], u * UNIT + w);
+                uint32_t vr;
+                node_in<RANGED>(p, nd[k][j], vr);
+                const Rec r = make_rec<TYPE>(f, nd[k] + w * NPE, i, t[k], u * UNIT + w, vr);
                 const uint32_t q = dof[dg[k][j]] + rk[k][j];
                 out[q] = make_ulonglong2(r.lo, r.hi);
                 odig[q] = dg[k][j];
@@ -555,35 +597,53 @@ __global__ void __launch_bounds__(OFFSETS_THREADS) k_offsets(OffsetsParams p) {
         }
         p.gcur[b] = (uint32_t)min(run, p.rec_cap);
         if (p.cshift > 0 && (b & ((1ll << p.cshift) - 1)) == 0) p.gcur_coarse[b >> p.cshift] = (uint32_t)min(run, p.rec_cap);
-        if (b == B - 1) p.bstart[B] = (uint32_t)min(run + tot, p.rec_cap);
+        if (b == B - 1) {
+            p.bstart[B] = (uint32_t)min(run + tot, p.rec_cap);
+            // more records than the record array holds: the record count the
+            // workspace was planned for was wrong (a chunk planned from stale
+            // counts); the partition stops at the array's end
+            if (run + tot > p.rec_cap) set_status(p.status, NN_ERR_WORKSPACE);
+        }
     }
 }
 
 template <int TYPE>
 cudaError_t hist_t(const EmitParams& p, size_t smem, cudaStream_t s) {
-    k_hist<TYPE><<<p.n_cta, EMIT_THREADS, smem, s>>>(p);
+    if (ranged(p)) k_hist<TYPE, true><<<p.n_cta, EMIT_THREADS, smem, s>>>(p);
+    else k_hist<TYPE, false><<<p.n_cta, EMIT_THREADS, smem, s>>>(p);
     return cudaGetLastError();
+}
+template <int TYPE, bool RANGED>
+void part_r(const EmitParams& p, cudaStream_t s) {
+    if (p.fmt.rb == 8) k_part<TYPE, 8, RANGED><<<p.n_cta_part, PART_THREADS, 0, s>>>(p);
+    else k_part<TYPE, 16, RANGED><<<p.n_cta_part, PART_THREADS, 0, s>>>(p);
 }
 template <int TYPE>
 cudaError_t part_t(const EmitParams& p, cudaStream_t s) {
-    if (p.fmt.rb == 8) k_part<TYPE, 8><<<p.n_cta_part, PART_THREADS, 0, s>>>(p);
-    else k_part<TYPE, 16><<<p.n_cta_part, PART_THREADS, 0, s>>>(p);
+    if (ranged(p)) part_r<TYPE, true>(p, s);
+    else part_r<TYPE, false>(p, s);
     return cudaGetLastError();
 }
 
 template <int TYPE>
 cudaError_t set_sorted_smem() {
-    cudaError_t e = cudaFuncSetAttribute(k_part_coarse<TYPE, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)coarse_smem<TYPE>());
+    const int b = (int)coarse_smem<TYPE>();
+    cudaError_t e = cudaFuncSetAttribute(k_part_coarse<TYPE, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_part_coarse<TYPE, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)coarse_smem<TYPE>());
+        e = cudaFuncSetAttribute(k_part_coarse<TYPE, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_part_coarse<TYPE, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_part_coarse<TYPE, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     return e;
 }
 
 template <int TYPE>
 cudaError_t set_emit_smem(size_t bytes) {
-    return cudaFuncSetAttribute(k_hist<TYPE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_hist<TYPE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_hist<TYPE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return e;
 }
 
 }  // namespace
@@ -608,11 +668,17 @@ cudaError_t launch_part(const EmitParams& p, cudaStream_t s) {
     }
 }
 
+template <int TYPE, bool RANGED>
+void coarse_r(const EmitParams& p, cudaStream_t s) {
+    const size_t smem = coarse_smem<TYPE>();
+    if (p.fmt.rb == 8) k_part_coarse<TYPE, 8, RANGED><<<p.n_cta_part, SORT_THREADS, smem, s>>>(p);
+    else k_part_coarse<TYPE, 16, RANGED><<<p.n_cta_part, SORT_THREADS, smem, s>>>(p);
+}
+
 template <int TYPE>
 cudaError_t part_sorted_t(const EmitParams& p, const uint32_t* bstart, int grid_fine, cudaStream_t s) {
-    const size_t smem = coarse_smem<TYPE>();
-    if (p.fmt.rb == 8) k_part_coarse<TYPE, 8><<<p.n_cta_part, SORT_THREADS, smem, s>>>(p);
-    else k_part_coarse<TYPE, 16><<<p.n_cta_part, SORT_THREADS, smem, s>>>(p);
+    if (ranged(p)) coarse_r<TYPE, true>(p, s);
+    else coarse_r<TYPE, false>(p, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || p.fmt.cshift <= 0) return e;
     const size_t fs = fine_smem(1 << p.fmt.cshift);
@@ -628,6 +694,23 @@ cudaError_t launch_part_sorted(const EmitParams& p, const uint32_t* bstart, int 
         case NN_TET: return part_sorted_t<NN_TET>(p, bstart, grid_fine, s);
         case NN_HEX: return part_sorted_t<NN_HEX>(p, bstart, grid_fine, s);
         default: return part_sorted_t<NN_MIXED>(p, bstart, grid_fine, s);
+    }
+}
+
+template <int TYPE>
+cudaError_t slab_count_t(const EmitParams& p, int shift, int n_slabs, uint32_t* counts, cudaStream_t s) {
+    k_slab_count<TYPE><<<p.n_cta, EMIT_THREADS, 0, s>>>(p, shift, n_slabs, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slab_count(const EmitParams& p, int shift, int n_slabs, uint32_t* counts, cudaStream_t s) {
+    if (n_slabs < 1 || n_slabs > NN_CHUNK_SLABS_MAX) return cudaErrorInvalidValue;
+    switch (p.type) {
+        case NN_TRI: return slab_count_t<NN_TRI>(p, shift, n_slabs, counts, s);
+        case NN_QUAD: return slab_count_t<NN_QUAD>(p, shift, n_slabs, counts, s);
+        case NN_TET: return slab_count_t<NN_TET>(p, shift, n_slabs, counts, s);
+        case NN_HEX: return slab_count_t<NN_HEX>(p, shift, n_slabs, counts, s);
+        default: return slab_count_t<NN_MIXED>(p, shift, n_slabs, counts, s);
     }
 }
 

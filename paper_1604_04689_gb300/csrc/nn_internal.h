@@ -43,6 +43,10 @@ struct EmitParams {
     const int64_t* elem_ptr;
     const uint8_t* elem_type;
     RecFmt fmt;
+    // node range of this build: incidences of nodes outside [node_lo,
+    // node_lo + node_span) are skipped, buckets count from node_lo (a whole
+    // mesh: 0 and n_nodes; a chunked build: one chunk)
+    int64_t node_lo, node_span;
     int64_t n_buckets;
     int64_t hist_chunk;  // buckets counted per walk of the histogram pass (shared counters)
     int n_cta;        // CTAs of the histogram pass (rows of hist)
@@ -132,6 +136,7 @@ struct BucketParams {
     int32_t wide;           // 1: 32 records and a 32-slot table per node in registers, 0: 16 and 16
     BatchTables batch;      // batch.hdr != nullptr: format, bucket count and meshes come from the tables
     const int32_t* batch_err;  // batches: status of the shared offsets scan, copied to every mesh
+    const int64_t* base;    // chunked builds: {element-CSR, node-CSR} entries of the earlier chunks (else nullptr)
 };
 
 constexpr int EMIT_THREADS = 1024;
@@ -155,6 +160,7 @@ struct CompactParams {
     int64_t* rp_n; int32_t* col_n; int64_t cap_n;
     int32_t* status;
     BatchTables batch;
+    const int64_t* base;     // chunked builds: {element-CSR, node-CSR} entries of the earlier chunks (else nullptr)
 };
 
 // Element face adjacency (nn_adj.cu).
@@ -177,6 +183,11 @@ struct AdjParams {
 cudaError_t launch_adjacency(const AdjParams& p, int grid, cudaStream_t s);
 size_t adjacency_scan_tiles(int64_t n_elems);
 cudaError_t launch_node_compact(const CompactParams& p, int copy_grid, cudaStream_t s);
+// chunked builds: base[0] += estart[B], base[1] += nstart[B] (either may be nullptr)
+cudaError_t launch_chunk_advance(int64_t* base, const uint32_t* estart, const uint64_t* nstart, int64_t B,
+                                 cudaStream_t s);
+// incidences per node slab of 2^shift nodes, added to counts[0 .. n_slabs) (n_slabs <= NN_CHUNK_SLABS_MAX)
+cudaError_t launch_slab_count(const EmitParams& p, int shift, int n_slabs, uint32_t* counts, cudaStream_t s);
 cudaError_t launch_hist(const EmitParams& p, size_t smem, cudaStream_t s);
 cudaError_t launch_part(const EmitParams& p, cudaStream_t s);
 cudaError_t launch_part_sorted(const EmitParams& p, const uint32_t* bstart, int grid_fine, cudaStream_t s);

@@ -6,7 +6,9 @@ PyTorch provides device memory and the stream.
 
 Low level (same names as the C ABI): ``nn_create``, ``nn_destroy``,
 ``nn_query``, ``nn_neighbor_nodes``, ``nn_neighbor_elements``,
-``nn_neighbors_both``, ``nn_status_str``.
+``nn_neighbors_both``, ``nn_chunk_slabs``, ``nn_chunk_count``,
+``nn_chunk_plan``, ``nn_neighbors_chunked``, ``nn_status_str`` and the rest
+of include/nn.h.
 
 High level: ``DeviceMesh`` (connectivity on the device) and ``Builder``,
 which sizes and allocates workspace and outputs with torch and returns CSR
@@ -49,6 +51,10 @@ class NNTuning(C.Structure):
     _fields_ = [("sb", C.c_int32), ("bucket_threads", C.c_int32), ("bucket_ctas_per_sm", C.c_int32)]
 
 
+class NNChunk(C.Structure):
+    _fields_ = [("node_lo", C.c_int64), ("node_hi", C.c_int64), ("records", C.c_int64)]
+
+
 class NNError(RuntimeError):
     def __init__(self, code: int, where: str = ""):
         self.code = code
@@ -70,6 +76,8 @@ def lib():
             P = C.c_void_p
             L.nn_create.argtypes = [C.POINTER(P)]
             L.nn_create.restype = C.c_int
+            L.nn_create_offline.argtypes = [C.POINTER(P), C.c_int32, C.c_int32, C.c_int32]
+            L.nn_create_offline.restype = C.c_int
             L.nn_destroy.argtypes = [P]
             L.nn_destroy.restype = None
             L.nn_query.argtypes = [P, C.POINTER(NNMesh), C.c_int, C.POINTER(C.c_size_t),
@@ -107,6 +115,18 @@ def lib():
             L.nn_generate_grid.argtypes = [C.c_int32, C.c_int64, C.c_uint64, C.c_int, C.c_int, P, C.c_int64,
                                            C.POINTER(C.c_int64), C.POINTER(C.c_int64), P]
             L.nn_generate_grid.restype = C.c_int
+            L.nn_chunk_slabs.argtypes = [C.POINTER(NNMesh), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+            L.nn_chunk_slabs.restype = C.c_int
+            L.nn_chunk_count.argtypes = [P, C.POINTER(NNMesh), P, P, P]
+            L.nn_chunk_count.restype = C.c_int
+            L.nn_chunk_plan.argtypes = [P, C.POINTER(NNMesh), C.c_int, P, C.c_size_t, P, C.c_int,
+                                        C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
+            L.nn_chunk_plan.restype = C.c_int
+            L.nn_chunk_query.argtypes = [P, C.POINTER(NNMesh), C.c_int, C.POINTER(NNChunk), C.POINTER(C.c_size_t)]
+            L.nn_chunk_query.restype = C.c_int
+            L.nn_neighbors_chunked.argtypes = [P, C.POINTER(NNMesh), C.c_int, P, C.c_int, C.POINTER(NNCSR),
+                                               C.POINTER(NNCSR), P, C.c_size_t, P, P]
+            L.nn_neighbors_chunked.restype = C.c_int
             L.nn_status_str.argtypes = [C.c_int]
             L.nn_status_str.restype = C.c_char_p
             _lib = L
@@ -120,6 +140,19 @@ def nn_create() -> int:
     st = lib().nn_create(C.byref(h))
     if st:
         raise NNError(st, "nn_create")
+    return h.value
+
+
+GB300_LIMITS = (152, 232448, 233472)   # SMs, opt-in shared memory per block, shared memory per SM
+
+
+def nn_create_offline(sms: int = GB300_LIMITS[0], smem_optin: int = GB300_LIMITS[1],
+                      smem_per_sm: int = GB300_LIMITS[2]) -> int:
+    """A sizing/planning-only handle for a described device (no GPU needed)."""
+    h = C.c_void_p()
+    st = lib().nn_create_offline(C.byref(h), sms, smem_optin, smem_per_sm)
+    if st:
+        raise NNError(st, "nn_create_offline")
     return h.value
 
 
@@ -188,6 +221,56 @@ def nn_element_neighbors_query(h: int, mesh: NNMesh):
 def nn_element_neighbors(h, mesh: NNMesh, node_elems: NNCSR, out: NNCSR, ws: int, ws_bytes: int, d_status: int,
                          stream: int) -> int:
     return lib().nn_element_neighbors(h, C.byref(mesh), C.byref(node_elems), C.byref(out), ws, ws_bytes, d_status,
+                                      stream)
+
+
+CHUNK_SLABS_MAX = 4096
+
+
+def nn_chunk_slabs(mesh: NNMesh):
+    """(shift, n_slabs): node slabs of 2^shift ids for the chunked build (host only)."""
+    sh = C.c_int()
+    ns = C.c_int()
+    st = lib().nn_chunk_slabs(C.byref(mesh), C.byref(sh), C.byref(ns))
+    if st:
+        raise NNError(st, "nn_chunk_slabs")
+    return sh.value, ns.value
+
+
+def nn_chunk_count(h: int, mesh: NNMesh, d_counts: int, d_status: int, stream: int) -> int:
+    """Enqueue the per-slab incidence count into device uint32 d_counts[n_slabs]."""
+    return lib().nn_chunk_count(h, C.byref(mesh), d_counts, d_status, stream)
+
+
+def nn_chunk_plan(h: int, mesh: NNMesh, want: int, counts, ws_bytes: int, max_chunks: int = 4096):
+    """Group slabs into chunks that fit ws_bytes (host only).  counts: sequence of
+    per-slab incidence counts.  Returns (status, [(node_lo, node_hi, records)], ws_needed)."""
+    arr = (C.c_uint32 * max(len(counts), 1))(*[int(c) for c in counts])
+    out = (NNChunk * max(max_chunks, 1))()
+    n = C.c_int()
+    need = C.c_size_t()
+    st = lib().nn_chunk_plan(h, C.byref(mesh), want, C.cast(arr, C.c_void_p), ws_bytes, C.cast(out, C.c_void_p),
+                             max_chunks, C.byref(n), C.byref(need))
+    chunks = [(out[i].node_lo, out[i].node_hi, out[i].records) for i in range(min(n.value, max_chunks))]
+    return st, chunks, need.value
+
+
+def nn_chunk_query(h: int, mesh: NNMesh, want: int, chunk) -> int:
+    """Workspace bytes of one chunk (node_lo, node_hi, records) (host only)."""
+    ws = C.c_size_t()
+    st = lib().nn_chunk_query(h, C.byref(mesh), want, C.byref(NNChunk(*chunk)), C.byref(ws))
+    if st:
+        raise NNError(st, "nn_chunk_query")
+    return ws.value
+
+
+def nn_neighbors_chunked(h: int, mesh: NNMesh, want: int, chunks, nodes: Optional[NNCSR],
+                         elems: Optional[NNCSR], ws: int, ws_bytes: int, d_status: int, stream: int) -> int:
+    """Enqueue the chunked build; chunks: [(node_lo, node_hi, records)] tiling [0, n_nodes)."""
+    arr = (NNChunk * max(len(chunks), 1))(*[NNChunk(*c) for c in chunks])
+    return lib().nn_neighbors_chunked(h, C.byref(mesh), want, C.cast(arr, C.c_void_p), len(chunks),
+                                      C.byref(nodes) if nodes is not None else None,
+                                      C.byref(elems) if elems is not None else None, ws, ws_bytes, d_status,
                                       stream)
 
 
@@ -411,6 +494,58 @@ class Builder:
                 raise NNError(status, "nn_element_neighbors (device)")
             break
         return rp, col[: int(rp[-1].item())]
+
+    def plan_chunks(self, dm: DeviceMesh, want: int, ws_bytes: int, stream=None):
+        """Count incidences per node slab on the device, wait for them, and
+        group the slabs into chunks whose workspace fits ws_bytes.  Returns
+        the chunk list [(node_lo, node_hi, records)]."""
+        torch = self.torch
+        mesh = dm.struct()
+        _, ns = nn_chunk_slabs(mesh)
+        counts = torch.zeros(max(ns, 1), dtype=torch.int32, device=self.device)
+        s = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        st = nn_chunk_count(self.h, mesh, counts.data_ptr(), self.status.data_ptr(), s)
+        if st:
+            raise NNError(st, "nn_chunk_count")
+        torch.cuda.synchronize(self.device)
+        if int(self.status.item()):
+            raise NNError(int(self.status.item()), "nn_chunk_count (device)")
+        host = [c & 0xFFFFFFFF for c in counts[:ns].cpu().tolist()]
+        st, chunks, need = nn_chunk_plan(self.h, mesh, want, host, ws_bytes)
+        if st:
+            raise NNError(st, f"nn_chunk_plan (smallest workspace {need} bytes)")
+        return chunks
+
+    def launch_chunked(self, dm: DeviceMesh, want: int, out: dict, chunks, ws, ws_bytes: int, stream=None,
+                       status=None) -> int:
+        """Enqueue a chunked build (no sync); returns the host status code."""
+        torch = self.torch
+        s = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+
+        def csr(key):
+            if key not in out:
+                return None
+            rp, col = out[key]
+            return NNCSR(rp.data_ptr(), col.data_ptr(), col.numel())
+        sp = (status if status is not None else self.status).data_ptr()
+        return nn_neighbors_chunked(self.h, dm.struct(), want, chunks, csr("nodes"), csr("elems"), ws.data_ptr(),
+                                    ws_bytes, sp, s)
+
+    def build_chunked(self, dm: DeviceMesh, want: int = WANT_BOTH, ws_bytes: int = 1 << 30):
+        """Like build, with the workspace capped at ws_bytes: nodes are built in
+        chunks of consecutive ids, each fitting the workspace."""
+        chunks = self.plan_chunks(dm, want, ws_bytes)
+        ws = self.torch.empty(max(ws_bytes, 256), dtype=self.torch.uint8, device=self.device)
+        out = self.alloc_outputs(dm, want)
+        st = self.launch_chunked(dm, want, out, chunks, ws, ws_bytes)
+        if st:
+            raise NNError(st, "nn_neighbors_chunked")
+        self.torch.cuda.synchronize(self.device)
+        res = {"status": int(self.status.item()), "chunks": chunks}
+        for k, (rp, col) in out.items():
+            nnz = int(rp[-1].item()) if res["status"] == 0 else col.numel()
+            res[k] = (rp, col[:nnz])
+        return res
 
     def build(self, dm: DeviceMesh, want: int = WANT_BOTH):
         """Build and return {'status': int, 'nodes': (row_ptr, col), 'elems': (row_ptr, col)} (col trimmed)."""
