@@ -8,7 +8,9 @@ processed per second, whole job).  Default workload: the 2048 x 2048
 triangle grid (4,194,304 nodes, 8,380,418 triangles, node ids and element
 order permuted).
 
-Prints ONE JSON line (rank 0).  See the design doc for the roofline accounting.
+Prints ONE JSON line (rank 0), with the roofline of the dominant kernel: its
+algorithmic bytes per launch (records read, CSRs written) over its CUDA-event
+time, against the measured copy bandwidth.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
 
@@ -28,16 +30,23 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    # name: (meshgen call, description)
-    "tri2048": ("config_mesh(1)", "triangle grid 2048x2048 (4,194,304 nodes, 8,380,418 tris), seed 1, "
-                                  "random diagonals, node ids and element order permuted"),
-    "tri2048_holes": ("config_mesh(1, 'holes')", "triangle grid 2048x2048 with 5% of triangles deleted, seed 100"),
-    "tet161": ("config_mesh(2)", "Kuhn tet grid 161^3 (4,173,281 nodes, 24,576,000 tets), seed 2, permuted"),
-    "hex257": ("config_mesh(3)", "hex grid 257^3 (16,974,593 nodes, 16,777,216 hexes), seed 3, node ids permuted"),
-    "mixed257": ("config_mesh(3, 'mixed')", "hex grid 257^3 with 30% of cells split into 6 tets, seed 103"),
-    "tri1448": ("tri_grid(1448, 5)", "triangle grid 1448x1448 (2,096,704 nodes, 4,187,618 tris), seed 5, "
-                                     "permuted (the profiling case: records exceed L2, a few hundred MB on the device)"),
-    "tri64": ("config_mesh(0)", "triangle grid 64x64 (4,096 nodes, 7,938 tris), seed 0, permuted"),
+    # name: (mesh generator, taking the meshgen module; description)
+    "tri2048": (lambda mg: mg.workload_mesh("tri2048"),
+                "triangle grid 2048x2048 (4,194,304 nodes, 8,380,418 tris), seed 1, "
+                "random diagonals, node ids and element order permuted"),
+    "tri2048_holes": (lambda mg: mg.workload_mesh("tri2048_holes"),
+                      "triangle grid 2048x2048 with 5% of triangles deleted, seed 100"),
+    "tet161": (lambda mg: mg.workload_mesh("tet161"),
+               "Kuhn tet grid 161^3 (4,173,281 nodes, 24,576,000 tets), seed 2, permuted"),
+    "hex257": (lambda mg: mg.workload_mesh("hex257"),
+               "hex grid 257^3 (16,974,593 nodes, 16,777,216 hexes), seed 3, node ids permuted"),
+    "mixed257": (lambda mg: mg.workload_mesh("mixed257"),
+                 "hex grid 257^3 with 30% of cells split into 6 tets, seed 103"),
+    "tri1448": (lambda mg: mg.tri_grid(1448, 5),
+                "triangle grid 1448x1448 (2,096,704 nodes, 4,187,618 tris), seed 5, permuted "
+                "(the profiling case: records exceed L2, a few hundred MB on the device)"),
+    "tri64": (lambda mg: mg.workload_mesh("tri64"),
+              "triangle grid 64x64 (4,096 nodes, 7,938 tris), seed 0, permuted"),
     "serve": (None, "stream of 10,000 mesh requests (tri / Kuhn tet / hex grids, elements log-uniform "
                     "1e3-2e6, per-request seeds), Poisson arrivals at 0.8x the plain saturated rate, "
                     "40 GB device-memory budget; batched continuous serving vs one build per mesh"),
@@ -84,8 +93,8 @@ def measured_peaks():
 
 
 def make_mesh(name):
-    from paper_1604_04689_gb300 import meshgen  # noqa: F401
-    return eval("meshgen." + WORKLOADS[name][0])
+    from paper_1604_04689_gb300 import meshgen
+    return WORKLOADS[name][0](meshgen)
 
 
 # ------------------------------------------------------------------ clocks

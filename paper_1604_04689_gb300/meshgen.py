@@ -286,22 +286,30 @@ def from_elements(elems, n_nodes: int, name: str = "") -> Mesh:
 
 # ---------------------------------------------------------------- workloads
 
-def config_mesh(k: int, variant: str = "") -> Mesh:
-    """The seeded synthetic workloads, by index.
+WORKLOAD_NAMES = ("tri64", "tri2048", "tri2048_holes", "tet161", "hex257", "mixed257")
 
-    0: tri 64x64 (seed 0); 1: tri 2048x2048 (seed 1; variant "holes": 5% of
-    elements deleted, seed 100); 2: Kuhn tet 161^3 (seed 2); 3: hex 257^3
-    (seed 3; variant "mixed": 30% of cells split into 6 tets, seed 103).
+
+def workload_mesh(name: str) -> Mesh:
+    """The seeded synthetic workloads, by name.
+
+    tri64: triangle grid 64x64 (seed 0); tri2048: triangle grid 2048x2048
+    (seed 1); tri2048_holes: the same grid with 5% of triangles deleted
+    (seed 100); tet161: Kuhn tet grid 161^3 (seed 2); hex257: hex grid 257^3
+    (seed 3); mixed257: hex257 with 30% of cells split into 6 tets (seed 103).
     """
-    if k == 0:
+    if name == "tri64":
         return tri_grid(64, 0)
-    if k == 1:
-        return tri_grid(2048, 100, holes=0.05) if variant == "holes" else tri_grid(2048, 1)
-    if k == 2:
+    if name == "tri2048":
+        return tri_grid(2048, 1)
+    if name == "tri2048_holes":
+        return tri_grid(2048, 100, holes=0.05)
+    if name == "tet161":
         return tet_grid(161, 2)
-    if k == 3:
-        return mixed_grid(257, 103) if variant == "mixed" else hex_grid(257, 3)
-    raise ValueError(k)
+    if name == "hex257":
+        return hex_grid(257, 3)
+    if name == "mixed257":
+        return mixed_grid(257, 103)
+    raise ValueError(f"unknown workload {name!r}; known: {', '.join(WORKLOAD_NAMES)}")
 
 
 def request_spec(i: int, base_seed: int = 4, lo: float = 1e3, hi: float = 2e6):

@@ -93,7 +93,7 @@ def test_capacity_error_reported():
 
 def test_full_size_tri2048():
     import torch
-    mesh = mg.config_mesh(1)
+    mesh = mg.workload_mesh("tri2048")
     rp, col = gpu_adjacency(mesh, nn.Builder())
     m = 2047
     assert int(rp[-1].item()) == 2 * ((2 * m * 2048 + m * m) - 4 * m)    # twice the interior edges

@@ -19,11 +19,11 @@ from tests.gpu_util import env
 pytestmark = pytest.mark.gpu
 
 WORKLOADS = {
-    "tri2048": (lambda: mg.config_mesh(1), 2 * pins.tri_grid_edges(2047)),
-    "tri2048_holes": (lambda: mg.config_mesh(1, "holes"), None),
-    "tet161": (lambda: mg.config_mesh(2), 2 * pins.kuhn_grid_edges(160)),
-    "hex257": (lambda: mg.config_mesh(3), 2 * pins.hex_grid_edges(256)),
-    "mixed257": (lambda: mg.config_mesh(3, "mixed"), None),
+    "tri2048": (lambda: mg.workload_mesh("tri2048"), 2 * pins.tri_grid_edges(2047)),
+    "tri2048_holes": (lambda: mg.workload_mesh("tri2048_holes"), None),
+    "tet161": (lambda: mg.workload_mesh("tet161"), 2 * pins.kuhn_grid_edges(160)),
+    "hex257": (lambda: mg.workload_mesh("hex257"), 2 * pins.hex_grid_edges(256)),
+    "mixed257": (lambda: mg.workload_mesh("mixed257"), None),
 }
 
 

@@ -57,7 +57,7 @@ MESHES = {
     "hex61": lambda: mg.hex_grid(61, 15),
     "hex37_elem_perm": lambda: mg.hex_grid(37, 16, permute_elems=True),
     "mixed41": lambda: mg.mixed_grid(41, 17),
-    "tri_config0": lambda: mg.config_mesh(0),
+    "tri64": lambda: mg.workload_mesh("tri64"),
 }
 
 

@@ -28,8 +28,8 @@ def test_splitmix64_reference_values():
     assert v.tolist() == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4]
 
 
-def test_config0_sizes():
-    m = mg.config_mesh(0)
+def test_tri64_sizes():
+    m = mg.workload_mesh("tri64")
     assert m.n_nodes == 4096 and m.n_elems == 7938 and m.conn.dtype == np.int32
     assert m.conn.min() == 0 and m.conn.max() == 4095
 
