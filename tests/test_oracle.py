@@ -84,6 +84,40 @@ def test_sort_restatement(mesh):
     np.testing.assert_array_equal(r["elems"][1], ecol)
 
 
+def random_soup(seed):
+    """Arbitrary connectivity: random element types, node ids drawn from a
+    small range so that elements repeat nodes (degenerate edges), share
+    nodes in no grid pattern, and leave some nodes untouched."""
+    rng = np.random.default_rng(seed)
+    n_nodes = int(rng.integers(1, 40))
+    elems = []
+    for _ in range(int(rng.integers(0, 30))):
+        t = int(rng.choice([mg.TRI, mg.QUAD, mg.TET, mg.HEX]))
+        elems.append((t, tuple(int(x) for x in rng.integers(0, n_nodes, mg.NPE[t]))))
+    if seed % 3 == 0 and elems:            # uniform type: the same element list, one type
+        t = elems[0][0]
+        elems = [(t, tuple(int(x) for x in rng.integers(0, n_nodes, mg.NPE[t]))) for _ in elems]
+    return mg.from_elements(elems, n_nodes, f"soup{seed}") if elems else \
+        mg.Mesh(mg.TRI, n_nodes, np.zeros(0, np.int32), name=f"soup{seed}")
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_soup_brute_force_and_sort(seed):
+    """Element soups with repeated and isolated nodes: the oracle equals the
+    geometric brute force and the paper's pair-sort recipe."""
+    mesh = random_soup(seed)
+    r = oracle.neighbors(mesh)
+    assert r["status"] == 0
+    bn, be = pins.brute_force(mesh.elements(), mesh.n_nodes)
+    assert pins.rows_of(*r["nodes"]) == bn
+    assert pins.rows_of(*r["elems"]) == be
+    (nrp, ncol), (erp, ecol) = pins.sort_restatement(mesh.elements(), mesh.n_nodes)
+    np.testing.assert_array_equal(r["nodes"][0], nrp)
+    np.testing.assert_array_equal(r["nodes"][1], ncol)
+    np.testing.assert_array_equal(r["elems"][0], erp)
+    np.testing.assert_array_equal(r["elems"][1], ecol)
+
+
 # ----------------------------------------------------------- closed forms
 
 def _coords2(n):
