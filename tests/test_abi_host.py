@@ -254,3 +254,57 @@ def test_missing_library_raises(monkeypatch, tmp_path):
         nn.lib()
     with pytest.raises(RuntimeError, match="not built"):
         nn.nn_create_offline()
+
+
+# ------------------------------------------------------------ build plan (host planner)
+
+PLAN_MESHES = {
+    "tri64": (nn.TRI, 4096, 7938),
+    "tri2048": (nn.TRI, 4_194_304, 8_380_418),
+    "tet161": (nn.TET, 4_173_281, 24_576_000),
+    "hex257": (nn.HEX, 16_974_593, 16_777_216),
+    "quad300": (nn.QUAD, 90_000, 89_401),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PLAN_MESHES))
+@pytest.mark.parametrize("want", [nn.WANT_NODES, nn.WANT_ELEMS, nn.WANT_BOTH])
+def test_plan_covers_the_nodes_and_holds_the_records(h, name, want):
+    etype, N, T = PLAN_MESHES[name]
+    m = uniform(etype, N, T)
+    p = nn.nn_plan_info(h, m, want)
+    ws, _, _ = nn.nn_query(h, m, want)
+    n_conn = nn.NPE[etype] * T
+    # the buckets tile [0, N): 2^sb consecutive ids each, the last one partial
+    assert 4 <= p["sb"] <= 11
+    assert (p["n_buckets"] - 1) << p["sb"] < N <= p["n_buckets"] << p["sb"]
+    # one packed record per incidence, 8 or 16 bytes, in the minimum workspace
+    assert p["record_bytes"] in (8, 16)
+    assert p["ws_min"] >= n_conn * p["record_bytes"]
+    # the recommended workspace adds a spill area of 16 MiB + 8 B per incidence
+    assert ws == p["ws_min"] + (16 << 20) + 8 * n_conn
+    # tile-sorted partition: one pass up to 256 buckets, else coarse regions of
+    # 2^k buckets, at most 256 of them and at most 4096 buckets each
+    if p["n_buckets"] <= 256:
+        assert p["partition"] == 0
+    else:
+        k = p["partition"]
+        assert 0 < k <= 12 and (p["n_buckets"] + (1 << k) - 1) >> k <= 256
+    assert p["bucket_threads"] in (128, 256)
+    assert 1 <= p["bucket_ctas"] <= p["n_buckets"]
+    assert p["bucket_smem"] <= 233472
+
+
+def test_record_width_follows_the_fields(h):
+    """Small meshes pack a record in 64 bits; the 2048^2 triangle grid (23-bit
+    element ids and two 23-bit neighbour fields) needs 128, unless only the
+    element rows are wanted (no neighbour fields)."""
+    assert nn.nn_plan_info(h, uniform(*PLAN_MESHES["tri64"]), nn.WANT_BOTH)["record_bytes"] == 8
+    assert nn.nn_plan_info(h, uniform(*PLAN_MESHES["tri2048"]), nn.WANT_BOTH)["record_bytes"] == 16
+    assert nn.nn_plan_info(h, uniform(*PLAN_MESHES["tri2048"]), nn.WANT_ELEMS)["record_bytes"] == 8
+
+
+def test_workspace_grows_with_the_mesh(h):
+    sizes = [nn.nn_query(h, uniform(nn.TET, 6 * n * n * n // 5, 6 * n * n * n), nn.WANT_BOTH)[0]
+             for n in (10, 40, 160)]
+    assert sizes[0] < sizes[1] < sizes[2]
