@@ -302,6 +302,20 @@ nn_status nn_profile_read(nn_handle* h, double* ms, int64_t* calls, int n_stages
 nn_status nn_neighbors_both_noalloc(const nn_mesh* mesh, nn_csr* nodes, nn_csr* elems, int32_t* d_status,
                                     nn_stream_t stream);
 
+/* Diagnostic of the bounded device-side waits; the paper has no counterpart.
+ * The single-pass scans of a build wait for predecessor tiles (a decoupled
+ * lookback).  Such a wait gives up after about 2 s without progress, writes
+ * NN_ERR_TIMEOUT to the call's status word and returns, so a lost
+ * predecessor never hangs the GPU.  This call runs that same wait for a tile
+ * whose predecessor never publishes, so that a test can watch it end.
+ * d_state: device, 3 x uint64, 8-byte aligned, overwritten: word 0 is the
+ * predecessor (set to 0, never published), word 1 receives the probed tile's
+ * published prefix when the wait ends, word 2 the wait's duration in ns.
+ * d_status: device int32, set to 0, then NN_ERR_TIMEOUT.  Asynchronous on
+ * stream; the kernel runs about 2 s.  Host errors: NN_ERR_ARG for a null or
+ * misaligned pointer, NN_ERR_CUDA if the launch fails. */
+nn_status nn_diag_wait_timeout(uint64_t* d_state, int32_t* d_status, nn_stream_t stream);
+
 /* Short English text for a status code (static storage). */
 const char* nn_status_str(nn_status s);
 

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libnn.so")
-SOURCES = ["nn_emit.cu", "nn_bucket.cu", "nn_batch.cu", "nn_compact.cu", "nn_adj.cu", "nn_api.cu", "nn_noalloc.cu", "nn_gen.cu"]
+SOURCES = ["nn_emit.cu", "nn_bucket.cu", "nn_batch.cu", "nn_compact.cu", "nn_adj.cu", "nn_api.cu", "nn_noalloc.cu",
+           "nn_gen.cu", "nn_diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

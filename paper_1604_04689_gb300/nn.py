@@ -127,6 +127,8 @@ def lib():
             L.nn_neighbors_chunked.argtypes = [P, C.POINTER(NNMesh), C.c_int, P, C.c_int, C.POINTER(NNCSR),
                                                C.POINTER(NNCSR), P, C.c_size_t, P, P]
             L.nn_neighbors_chunked.restype = C.c_int
+            L.nn_diag_wait_timeout.argtypes = [P, P, P]
+            L.nn_diag_wait_timeout.restype = C.c_int
             L.nn_status_str.argtypes = [C.c_int]
             L.nn_status_str.restype = C.c_char_p
             _lib = L
@@ -280,6 +282,11 @@ NOALLOC_SCRATCH_BYTES = 32 << 20
 def nn_neighbors_both_noalloc(mesh: NNMesh, nodes: NNCSR, elems: NNCSR, d_status: int, stream: int) -> int:
     """Both CSRs with the library's fixed device scratch instead of a workspace (allocates nothing)."""
     return lib().nn_neighbors_both_noalloc(C.byref(mesh), C.byref(nodes), C.byref(elems), d_status, stream)
+
+
+def nn_diag_wait_timeout(d_state: int, d_status: int, stream: int) -> int:
+    """Run one bounded lookback wait whose predecessor never publishes (see include/nn.h)."""
+    return lib().nn_diag_wait_timeout(d_state, d_status, stream)
 
 
 def nn_batch_query(h: int, caps: NNBatchCaps):

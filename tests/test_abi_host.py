@@ -308,3 +308,13 @@ def test_workspace_grows_with_the_mesh(h):
     sizes = [nn.nn_query(h, uniform(nn.TET, 6 * n * n * n // 5, 6 * n * n * n), nn.WANT_BOTH)[0]
              for n in (10, 40, 160)]
     assert sizes[0] < sizes[1] < sizes[2]
+
+
+def test_wait_probe_checks_its_pointers_on_the_host():
+    """The bounded-wait diagnostic rejects null and misaligned pointers before
+    touching the device."""
+    L = nn.lib()
+    assert L.nn_diag_wait_timeout(None, FAKE, None) == ARG
+    assert L.nn_diag_wait_timeout(FAKE, None, None) == ARG
+    assert L.nn_diag_wait_timeout(FAKE + 4, FAKE, None) == ARG
+    assert L.nn_diag_wait_timeout(FAKE, FAKE + 2, None) == ARG
