@@ -12,6 +12,10 @@ separate restatements used to pin the oracle down.
 * ``sort_restatement``: the paper's own GPU recipe run with numpy on the CPU
   (Sec. 2.2: emit integer pairs, sort by key, segment by key), plus removal
   of repeated pairs so rows are sets.
+* ``brute_force_faces``: element face adjacency over all element pairs,
+  with faces derived geometrically too: edges of a triangle or quad (the
+  sides), 3-subsets of a tet, and hex corners sharing one unit-cube
+  coordinate value.
 * closed forms for structured grids and the per-node triangle identity.
 """
 from __future__ import annotations
@@ -36,6 +40,34 @@ def local_edges(etype: int):
         return [(i, j) for i, j in itertools.combinations(range(8), 2)
                 if sum(abs(a - b) for a, b in zip(HEX_XYZ[i], HEX_XYZ[j])) == 1]
     raise ValueError(etype)
+
+
+def local_faces(etype: int):
+    """Local faces derived from the element's shape (not copied from a table):
+    the sides of a polygon, the vertex triples of a tet, the six sets of hex
+    corners that agree in one unit-cube coordinate."""
+    if etype in (0, 1):   # polygon: its sides are its edges
+        return local_edges(etype)
+    if etype == 2:
+        return list(itertools.combinations(range(4), 3))
+    if etype == 3:
+        return [tuple(i for i in range(8) if HEX_XYZ[i][d] == c) for d in range(3) for c in (0, 1)]
+    raise ValueError(etype)
+
+
+def brute_force_faces(elements):
+    """Rows of element face neighbours: e != f are neighbours iff every node of
+    some face of one of them (a face whose nodes are all distinct) is a node
+    of the other."""
+    faces = [[frozenset(nd[i] for i in fc) for fc in local_faces(t) if len({nd[i] for i in fc}) == len(fc)]
+             for t, nd in elements]
+    nodes = [set(nd) for _, nd in elements]
+    rows = [[] for _ in elements]
+    for e, f in itertools.combinations(range(len(elements)), 2):
+        if any(fc <= nodes[f] for fc in faces[e]) or any(fc <= nodes[e] for fc in faces[f]):
+            rows[e].append(f)
+            rows[f].append(e)
+    return rows
 
 
 def brute_force(elements, n_nodes):

@@ -2,8 +2,9 @@
 tables: closed-form interior-face counts of the structured grids, interior
 element degrees, neighbours from cell coordinates (quad and hex grids), the
 shared-vertex rule for conforming simplices, a hand-derived mixed fixture (a
-hex next to a cell split into Kuhn tets), degenerate elements, and mutants of
-the oracle source that these pins must catch."""
+hex next to a cell split into Kuhn tets), degenerate elements, a pairwise
+brute force with geometrically derived faces on grids and random element
+soups, and mutants of the oracle source that these pins must catch."""
 import os
 import subprocess
 import sys
@@ -15,6 +16,8 @@ import pytest
 
 import oracle
 from paper_1604_04689_gb300 import meshgen as mg
+from tests import pins
+from tests.test_oracle import random_soup
 
 
 _LIB = [None]   # oracle build the pins run against (a mutant's, in the mutant test)
@@ -150,6 +153,21 @@ def test_sample_rows_equal_full_rows():
     assert [col[rp[i]:rp[i + 1]].tolist() for i in range(len(sample))] == [full[e] for e in sample]
 
 
+@pytest.mark.parametrize("seed", range(40))
+def test_random_soup_brute_force(seed):
+    """Element soups (random types, repeated and shared nodes in no grid
+    pattern): the oracle equals the pairwise brute force with geometric faces."""
+    mesh = random_soup(seed)
+    assert adj_rows(mesh) == pins.brute_force_faces(mesh.elements())
+
+
+@pytest.mark.parametrize("mesh", [mg.mixed_grid(4, 11, frac_tet=0.5), mg.tri_grid(7, 9, holes=0.2),
+                                  mg.hex_grid(4, 6), mg.quad_grid(5, 3), mg.tet_grid(3, 4)],
+                         ids=lambda m: m.name)
+def test_grid_brute_force(mesh):
+    assert adj_rows(mesh) == pins.brute_force_faces(mesh.elements())
+
+
 MUTANTS = {
     # both y-faces (one hex's y = 0 face is its neighbour's y = 1 face, and the
     # test runs both ways, so one wrong face alone changes nothing)
@@ -171,6 +189,13 @@ def _adj_pin_failures(lib):
                 failed.append("closed:" + kind)
         except Exception:
             failed.append("closed:" + kind)
+    for seed in range(20):
+        mesh = random_soup(seed)
+        try:
+            if adj_rows(mesh, lib) != pins.brute_force_faces(mesh.elements()):
+                failed.append(f"soup:{seed}")
+        except Exception:
+            failed.append(f"soup:{seed}")
     for name, fn in (("split", test_hex_next_to_split_cell), ("degenerate", test_degenerate_elements)):
         _LIB[0] = lib
         try:
@@ -196,6 +221,9 @@ def test_pins_catch_adjacency_mutants():
             subprocess.check_call(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", path, "-o", so])
             code = ("import sys, oracle; from tests.test_oracle_adjacency import _adj_pin_failures; "
                     f"sys.exit(0 if not _adj_pin_failures(oracle.load_library({so!r})) else 3)")
-            rc = subprocess.run([sys.executable, "-c", code], cwd=root,
-                                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL).returncode
+            try:   # a mutant that crashes or never ends counts as caught
+                rc = subprocess.run([sys.executable, "-c", code], cwd=root, stdout=subprocess.DEVNULL,
+                                    stderr=subprocess.DEVNULL, timeout=20).returncode
+            except subprocess.TimeoutExpired:
+                rc = "hung"
             assert rc != 0, f"mutant {name} survived the pins"
