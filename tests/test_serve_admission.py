@@ -41,3 +41,20 @@ def test_admission_stops_at_first_misfit_and_rejects_oversize():
     q = deque([small, mid, Request(3, mg.TRI, 20, 2, 0.0), small])
     b = adm.form(q, 1 << 40)
     assert [r.rid for r in b] == [0, 2] and [r.rid for r in q] == [3, 0]              # 722+1682+722 > 3000
+
+
+def test_request_bytes_cover_the_library_bounds():
+    """What admission counts per request is the connectivity plus both CSRs at
+    the library's own capacity bounds (nn_query on an offline handle), so a
+    batch admitted under the budget can always hold its results."""
+    from paper_1604_04689_gb300 import build, nn
+    build.build()
+    h = nn.nn_create_offline()
+    try:
+        for t, n in ((mg.TRI, 40), (mg.QUAD, 17), (mg.TET, 9), (mg.HEX, 11)):
+            r = Request(0, t, n, 1, 0.0)
+            s = nn.NNMesh(t, r.n_nodes, r.n_elems, r.n_conn, 1 << 20, None, None)
+            _, node_cap, elem_cap = nn.nn_query(h, s, nn.WANT_BOTH)
+            assert r.device_bytes() == 4 * r.n_conn + 2 * 8 * (r.n_nodes + 1) + 4 * (node_cap + elem_cap)
+    finally:
+        nn.nn_destroy(h)
