@@ -259,6 +259,25 @@ nn_status nn_batch_prepare(nn_handle* h, const nn_batch_caps* caps, const nn_mes
 nn_status nn_batch_launch(nn_handle* h, const nn_batch_caps* caps, const void* staging, void* ws,
                           size_t ws_bytes, nn_stream_t stream);
 
+/* One-call batch (the same results as the three calls above), for callers
+ * that do not capture graphs.  Builds the n_meshes meshes into their own
+ * outputs with one launch sequence.  The wanted results are the non-NULL
+ * ones of node_out / elem_out (arrays of n_meshes CSRs; at least one must be
+ * given).  The capacity is the meshes' own totals: size ws with
+ * nn_batch_submit_query for the same meshes and want.  ws: device memory,
+ * 256-byte aligned.  d_status: device int32[n_meshes], one status word per
+ * mesh, as in nn_batch_prepare.  The batch description is staged in host
+ * memory that the call allocates; the stream frees it after the batch has
+ * run (a host function enqueued on `stream`).  So the call is asynchronous
+ * but cannot be captured in a CUDA graph: use nn_batch_prepare /
+ * nn_batch_launch for that.  n_meshes == 0 enqueues nothing.  Host errors:
+ * NN_ERR_ARG (bad mesh or pointers, no output wanted), NN_ERR_WORKSPACE
+ * (ws_bytes below the minimum), NN_ERR_BUDGET (host memory for the staging
+ * exhausted), NN_ERR_CUDA. */
+nn_status nn_batch_submit_query(nn_handle* h, const nn_mesh* meshes, int n_meshes, int want, size_t* ws_bytes);
+nn_status nn_batch_submit(nn_handle* h, const nn_mesh* meshes, nn_csr* node_out, nn_csr* elem_out, int n_meshes,
+                          void* ws, size_t ws_bytes, int32_t* d_status, nn_stream_t stream);
+
 /* Seeded synthetic grid meshes generated on the device -- input generation
  * for benchmarks and the serving loop, not part of the method.  The result is
  * identical to the host generator (paper_1604_04689_gb300/meshgen.py):

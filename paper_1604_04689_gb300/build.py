@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libnn.so")
 SOURCES = ["nn_emit.cu", "nn_bucket.cu", "nn_batch.cu", "nn_compact.cu", "nn_adj.cu", "nn_api.cu", "nn_noalloc.cu",
-           "nn_gen.cu", "nn_diag.cu"]
+           "nn_gen.cu", "nn_diag.cu", "nn_submit.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

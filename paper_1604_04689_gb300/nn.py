@@ -127,6 +127,10 @@ def lib():
             L.nn_neighbors_chunked.argtypes = [P, C.POINTER(NNMesh), C.c_int, P, C.c_int, C.POINTER(NNCSR),
                                                C.POINTER(NNCSR), P, C.c_size_t, P, P]
             L.nn_neighbors_chunked.restype = C.c_int
+            L.nn_batch_submit_query.argtypes = [P, P, C.c_int, C.c_int, C.POINTER(C.c_size_t)]
+            L.nn_batch_submit_query.restype = C.c_int
+            L.nn_batch_submit.argtypes = [P, P, P, P, C.c_int, P, C.c_size_t, P, P]
+            L.nn_batch_submit.restype = C.c_int
             L.nn_diag_wait_timeout.argtypes = [P, P, P]
             L.nn_diag_wait_timeout.restype = C.c_int
             L.nn_status_str.argtypes = [C.c_int]
@@ -282,6 +286,21 @@ NOALLOC_SCRATCH_BYTES = 32 << 20
 def nn_neighbors_both_noalloc(mesh: NNMesh, nodes: NNCSR, elems: NNCSR, d_status: int, stream: int) -> int:
     """Both CSRs with the library's fixed device scratch instead of a workspace (allocates nothing)."""
     return lib().nn_neighbors_both_noalloc(C.byref(mesh), C.byref(nodes), C.byref(elems), d_status, stream)
+
+
+def nn_batch_submit_query(h: int, meshes, n: int, want: int) -> int:
+    """Workspace bytes of a one-call batch of these meshes (an array of NNMesh)."""
+    ws = C.c_size_t()
+    st = lib().nn_batch_submit_query(h, meshes, n, want, C.byref(ws))
+    if st:
+        raise NNError(st, "nn_batch_submit_query")
+    return ws.value
+
+
+def nn_batch_submit(h: int, meshes, node_out, elem_out, n: int, ws: int, ws_bytes: int, d_status: int,
+                    stream: int) -> int:
+    """One-call batch: arrays of NNMesh and NNCSR (either output array may be None)."""
+    return lib().nn_batch_submit(h, meshes, node_out, elem_out, n, ws, ws_bytes, d_status, stream)
 
 
 def nn_diag_wait_timeout(d_state: int, d_status: int, stream: int) -> int:

@@ -318,3 +318,23 @@ def test_wait_probe_checks_its_pointers_on_the_host():
     assert L.nn_diag_wait_timeout(FAKE, None, None) == ARG
     assert L.nn_diag_wait_timeout(FAKE + 4, FAKE, None) == ARG
     assert L.nn_diag_wait_timeout(FAKE, FAKE + 2, None) == ARG
+
+
+def test_batch_submit_host_rules(h):
+    """The one-call batch sizes its workspace as the three-step batch does for
+    the meshes' totals, and refuses bad requests before touching the device."""
+    L = nn.lib()
+    ms = [uniform(nn.TRI, 100, 150), uniform(nn.HEX, 64, 27), uniform(nn.TET, 50, 120)]
+    arr = (nn.NNMesh * 3)(*ms)
+    ws = nn.nn_batch_submit_query(h, arr, 3, nn.WANT_BOTH)
+    caps = nn.NNBatchCaps(3, nn.WANT_BOTH, sum(m.n_elems for m in ms), sum(m.n_nodes for m in ms),
+                          sum(m.n_conn for m in ms), 0)
+    assert ws == nn.nn_batch_query(h, caps)[0]
+    outs = (nn.NNCSR * 3)(*[nn.NNCSR(FAKE, FAKE, 10_000) for _ in ms])
+    assert L.nn_batch_submit(h, arr, None, None, 3, FAKE, ws, FAKE, None) == ARG       # no output wanted
+    assert L.nn_batch_submit(h, arr, outs, outs, 3, FAKE, ws, FAKE, None) == ARG       # offline handle
+    assert L.nn_batch_submit(h, arr, outs, outs, 0, FAKE, ws, FAKE, None) == 0         # nothing to do
+    assert L.nn_batch_submit(h, None, outs, outs, 2, FAKE, ws, FAKE, None) == ARG
+    bad = (nn.NNMesh * 1)(uniform(nn.TRI, -1, 2))
+    with pytest.raises(nn.NNError):
+        nn.nn_batch_submit_query(h, bad, 1, nn.WANT_BOTH)

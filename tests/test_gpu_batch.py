@@ -138,3 +138,56 @@ def test_capacity_is_checked_on_the_host():
     assert bb.prepare(dms, [bb.alloc_outputs(d) for d in dms]) == 7     # NN_ERR_BUDGET
     small = nn.BatchBuilder(max_meshes=2, max_elems=10**6, max_nodes=10**6, max_conn=10**6)
     assert small.prepare(dms, [small.alloc_outputs(d) for d in dms]) == 1   # more meshes than slots
+
+
+@pytest.mark.parametrize("want", [nn.WANT_BOTH, nn.WANT_NODES, nn.WANT_ELEMS])
+def test_one_call_submit_equals_the_oracle(want):
+    """nn_batch_submit: two batches enqueued back to back on one stream (the
+    first one's staging is still in use when the second is prepared), each
+    mesh's CSRs equal to the oracle's."""
+    import torch
+    h = nn.nn_create()
+    try:
+        stream = torch.cuda.current_stream().cuda_stream
+        runs = []
+        for meshes in (batch_meshes(7)[:14], batch_meshes(8)[2:12]):
+            dms = [nn.DeviceMesh.from_host(m) for m in meshes]
+            n = len(dms)
+            arr = (nn.NNMesh * n)(*[d.struct() for d in dms])
+            ws_bytes = nn.nn_batch_submit_query(h, arr, n, want)
+            ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+            status = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+            outs = []
+            for d in dms:
+                o = {}
+                if want & nn.WANT_NODES:
+                    k = 2 if d.etype in (nn.TRI, nn.QUAD) else 3
+                    o["nodes"] = (torch.empty(d.n_nodes + 1, dtype=torch.int64, device="cuda"),
+                                  torch.empty(max(k * d.n_conn, 1), dtype=torch.int32, device="cuda"))
+                if want & nn.WANT_ELEMS:
+                    o["elems"] = (torch.empty(d.n_nodes + 1, dtype=torch.int64, device="cuda"),
+                                  torch.empty(max(d.n_conn, 1), dtype=torch.int32, device="cuda"))
+                outs.append(o)
+
+            def csrs(key):
+                if key not in outs[0]:
+                    return None
+                return (nn.NNCSR * n)(*[nn.NNCSR(o[key][0].data_ptr(), o[key][1].data_ptr(), o[key][1].numel())
+                                        for o in outs])
+            node_arr, elem_arr = csrs("nodes"), csrs("elems")
+            st = nn.nn_batch_submit(h, arr, node_arr, elem_arr, n, ws.data_ptr(), ws_bytes, status.data_ptr(),
+                                    stream)
+            assert st == 0, nn.STATUS.get(st, st)
+            runs.append((meshes, dms, outs, status, ws, arr, node_arr, elem_arr))
+        torch.cuda.synchronize()
+        for meshes, _, outs, status, *_ in runs:
+            assert status.cpu().tolist() == [0] * len(meshes)
+            for m, o in zip(meshes, outs):
+                ref = oracle.neighbors(m, want)
+                for key, (rp, col) in o.items():
+                    rp = rp.cpu().numpy()
+                    np.testing.assert_array_equal(rp, ref[key][0], err_msg=f"{m.name} {key} row_ptr")
+                    np.testing.assert_array_equal(col.cpu().numpy()[: rp[-1]], ref[key][1],
+                                                  err_msg=f"{m.name} {key} col")
+    finally:
+        nn.nn_destroy(h)
