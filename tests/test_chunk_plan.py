@@ -127,3 +127,48 @@ def test_offline_handle_refuses_compute(h):
                                    FAKE, 0) == 1
     with pytest.raises(nn.NNError):
         nn.nn_create_offline(0, 1 << 17, 1 << 17)
+
+
+def random_counts(seed, ns):
+    """Slab-count profiles a grid never gives: empty slabs, one hub slab
+    holding a large share, heavy tails."""
+    rng = np.random.default_rng(seed)
+    kind = seed % 3
+    if kind == 0:
+        c = rng.integers(0, 5000, ns)
+        c[rng.random(ns) < 0.3] = 0
+    elif kind == 1:
+        c = rng.integers(0, 200, ns)
+        c[int(rng.integers(ns))] = 400_000
+    else:
+        c = (rng.pareto(1.2, ns) * 300).astype(np.int64)
+    return c.astype(np.int64)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_plan_on_random_slab_profiles(h, seed):
+    N = int(np.random.default_rng(100 + seed).integers(5_000, 3_000_000))
+    probe = nn.NNMesh(nn.TRI, N, 0, 0, None, None, None)
+    shift, ns = nn.nn_chunk_slabs(probe)
+    counts = random_counts(seed, ns)
+    total = int(counts.sum())
+    T = (total + 2) // 3
+    s = nn.NNMesh(nn.TRI, N, T, 3 * T, FAKE if T else None, None, None)
+    st, one, need = nn.nn_chunk_plan(h, s, nn.WANT_BOTH, counts, 1 << 42)
+    assert st == 0 and one == [(0, N, total)]
+    assert nn.nn_chunk_plan(h, s, nn.WANT_BOTH, counts, need - 1)[0] == 2     # below the largest slab
+    prev = None
+    for ws in (need, need + (need >> 1), 2 * need, 4 * need):
+        st, chunks, _ = nn.nn_chunk_plan(h, s, nn.WANT_BOTH, counts, ws)
+        assert st == 0
+        assert chunks[0][0] == 0 and chunks[-1][1] == N
+        assert all(a[1] == b[0] for a, b in zip(chunks, chunks[1:]))
+        for lo, hi, rec in chunks:
+            assert lo % (1 << shift) == 0
+            assert rec == int(counts[lo >> shift: (hi + (1 << shift) - 1) >> shift].sum())
+            assert nn.nn_chunk_query(h, s, nn.WANT_BOTH, (lo, hi, rec)) <= ws
+            if hi < N:
+                grown = (lo, min(N, hi + (1 << shift)), rec + int(counts[hi >> shift]))
+                assert nn.nn_chunk_query(h, s, nn.WANT_BOTH, grown) > ws
+        assert prev is None or len(chunks) <= prev
+        prev = len(chunks)
