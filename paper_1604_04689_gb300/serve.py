@@ -80,6 +80,20 @@ class LaneCaps:
     max_conn: int = 64_000_000
 
 
+class ServeTimeout(RuntimeError):
+    """A batch (or a plain build) whose completion event did not fire within
+    the host deadline.  The device kernels bound their own waits, so this is
+    a backstop: the loop stops with an error instead of polling forever."""
+
+
+def check_deadline(t_launch: float, deadline_s: float, what: str, now: Optional[float] = None) -> None:
+    """Raise ServeTimeout if ``what``, enqueued at host time ``t_launch``, is
+    still running ``deadline_s`` seconds later."""
+    now = time.perf_counter() if now is None else now
+    if now - t_launch > deadline_s:
+        raise ServeTimeout(f"{what} not complete {now - t_launch:.1f} s after launch (deadline {deadline_s} s)")
+
+
 class Admission:
     """Which waiting requests go into the next batch (host logic only).
 
@@ -124,6 +138,7 @@ class _Lane:
         self.ev_start = torch.cuda.Event(enable_timing=True)
         self.reqs = None
         self.bufs = None
+        self.t_launch = 0.0    # host time the lane's current batch was enqueued
 
     def workspace_bytes(self) -> int:
         return self.bb.ws_bytes
@@ -179,10 +194,12 @@ def _stats(reqs: List[Request], t_first: float, t_last: float) -> dict:
 
 class BatchServer:
     def __init__(self, budget_bytes: int = 40 << 30, lanes: int = 2, caps: Optional[LaneCaps] = None,
-                 want: int = nn.WANT_BOTH, device=None, use_graph: bool = True, keep_results: bool = False):
+                 want: int = nn.WANT_BOTH, device=None, use_graph: bool = True, keep_results: bool = False,
+                 deadline_s: float = 60.0):
         import torch
         self.torch = torch
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.deadline_s = deadline_s
         self.caps = caps or LaneCaps()
         self.want = want
         self.keep = keep_results
@@ -224,6 +241,7 @@ class BatchServer:
                     lane.reqs = lane.bufs = None
                     free.append(lane)
                 else:
+                    check_deadline(lane.t_launch, self.deadline_s, f"batch of {len(lane.reqs)} requests")
                     still.append(lane)
             busy = still
             if free and queue:
@@ -238,6 +256,7 @@ class BatchServer:
                     if st:
                         raise nn.NNError(st, "nn_batch_prepare")
                     lane.ev_start.record(lane.stream)
+                    lane.t_launch = time.perf_counter()
                     lane.launch()
                     lane.event.record(lane.stream)
                     lane.reqs, lane.bufs = batch, bufs
@@ -259,10 +278,12 @@ class BatchServer:
 class PlainServer:
     """One nn_neighbors_both call per request, in arrival order, on one stream."""
 
-    def __init__(self, max_request: Request, want: int = nn.WANT_BOTH, device=None, keep_results: bool = False):
+    def __init__(self, max_request: Request, want: int = nn.WANT_BOTH, device=None, keep_results: bool = False,
+                 deadline_s: float = 60.0):
         import torch
         self.torch = torch
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.deadline_s = deadline_s
         self.b = nn.Builder(self.device)
         self.stream = torch.cuda.Stream(self.device)
         self.want = want
@@ -285,7 +306,7 @@ class PlainServer:
         while pending or inflight:
             now = time.perf_counter() - t0
             while inflight and inflight[0][1].query():
-                r, ev, out, ev_s = inflight.popleft()
+                r, ev, out, ev_s, _ = inflight.popleft()
                 r.t_done = ev0.elapsed_time(ev) * 1e-3
                 r.t_start = ev0.elapsed_time(ev_s) * 1e-3
                 if self.keep:
@@ -303,9 +324,10 @@ class PlainServer:
                     raise nn.NNError(st_, "plain build")
                 ev = torch.cuda.Event(enable_timing=True)
                 ev.record(self.stream)
-                inflight.append((r, ev, out, ev_s))
+                inflight.append((r, ev, out, ev_s, time.perf_counter()))
                 continue
             if inflight:
+                check_deadline(inflight[0][4], self.deadline_s, f"build of request {inflight[0][0].rid}")
                 time.sleep(20e-6)
             elif pending:
                 time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 0.001)))

@@ -1,0 +1,163 @@
+"""The serving loops' host logic on the CPU: BatchServer and PlainServer run
+their real event loops against fake CUDA streams, events and builders (each
+"GPU" batch completes a fixed time after it is enqueued), so admission across
+lanes, completion bookkeeping, rejection of oversized requests and the
+statistics are checked without a GPU; and a stream that never completes
+trips the host watchdog instead of spinning forever."""
+import contextlib
+import time
+
+import pytest
+import torch
+
+from paper_1604_04689_gb300 import meshgen as mg
+from paper_1604_04689_gb300 import nn, serve
+from paper_1604_04689_gb300.serve import BatchServer, LaneCaps, PlainServer, Request
+
+GPU_S = 0.002        # simulated device time of one enqueued batch or build
+
+
+class FakeStream:
+    hang = False     # set on the class by a test: nothing recorded on any stream ever completes
+
+    def __init__(self, device=None):
+        self.cuda_stream = 0
+        self.busy_until = 0.0
+
+    def enqueue(self):
+        self.busy_until = max(self.busy_until, time.perf_counter()) + GPU_S
+
+
+class FakeEvent:
+    def __init__(self, enable_timing=False):
+        self.t = None
+
+    def record(self, stream=None):
+        s = stream if stream is not None else _DEFAULT
+        self.t = float("inf") if FakeStream.hang and s is not _DEFAULT else max(s.busy_until, time.perf_counter())
+
+    def query(self):
+        return self.t is not None and time.perf_counter() >= self.t
+
+    def elapsed_time(self, other):
+        return (other.t - self.t) * 1e3
+
+
+_DEFAULT = FakeStream()
+
+
+class FakeBatchBuilder:
+    launches = 0
+
+    def __init__(self, max_meshes, max_elems, max_nodes, max_conn, want=nn.WANT_BOTH, device=None, **kw):
+        self.ws_bytes = 1 << 20
+        self.status = torch.zeros(max_meshes, dtype=torch.int32)
+        self.n = 0
+
+    def prepare(self, dmeshes, outs):
+        self.n = len(dmeshes)
+        return 0
+
+    def launch(self, stream):
+        FakeBatchBuilder.launches += 1
+        stream.enqueue()
+        return 0
+
+
+class FakeBuilder:
+    def __init__(self, device=None):
+        pass
+
+    def query(self, dm, want):
+        return 1 << 20, 0, 0
+
+    def workspace(self, nbytes):
+        return torch.empty(16, dtype=torch.uint8)
+
+    def launch(self, dm, want, out, ws=None, ws_bytes=None, stream=None, status=None):
+        stream.enqueue()
+        return 0
+
+
+def fake_generate_grid(etype, n, seed, permute_nodes=True, permute_elems=None, device=None, stream=None):
+    return nn.DeviceMesh(etype, 0, torch.zeros(0, dtype=torch.int32))
+
+
+@pytest.fixture
+def fake_cuda(monkeypatch):
+    monkeypatch.setattr(torch.cuda, "Stream", FakeStream)
+    monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
+    monkeypatch.setattr(torch.cuda, "current_stream", lambda device=None: _DEFAULT)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda device=None: None)
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
+    monkeypatch.setattr(nn, "BatchBuilder", FakeBatchBuilder)
+    monkeypatch.setattr(nn, "Builder", FakeBuilder)
+    monkeypatch.setattr(nn, "generate_grid", fake_generate_grid)
+    FakeStream.hang = False
+    FakeBatchBuilder.launches = 0
+    yield
+    FakeStream.hang = False
+
+
+def small_requests(n, rate=2000.0):
+    """Tiny grids (so the CPU output buffers stay small), arriving at ``rate``."""
+    reqs = []
+    for i in range(n):
+        t = (mg.TRI, mg.TET, mg.HEX)[i % 3]
+        reqs.append(Request(i, t, 3 + i % 4, i, i / rate))
+    return reqs
+
+
+def test_batch_server_serves_every_request(fake_cuda):
+    reqs = small_requests(40)
+    srv = BatchServer(budget_bytes=1 << 30, lanes=2, caps=LaneCaps(max_meshes=8), device="cpu", use_graph=False)
+    st = srv.run(reqs)
+    assert st["requests"] == 40 and st["failed"] == 0 and st["rejected"] == 0
+    assert all(r.t_done >= r.arrival for r in reqs)           # completion after arrival
+    assert all(r.t_done >= r.t_start >= 0 for r in reqs)
+    assert st["batches"] == FakeBatchBuilder.launches and 5 <= st["batches"] <= 40   # at most 8 per batch
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+
+
+def test_batch_server_rejects_what_no_lane_holds(fake_cuda):
+    reqs = small_requests(6)
+    reqs.append(Request(6, mg.TRI, 200, 1, 0.001))            # 79,202 triangles: more than a lane's capacity
+    srv = BatchServer(budget_bytes=1 << 30, lanes=2, caps=LaneCaps(max_meshes=4, max_elems=10_000), device="cpu",
+                      use_graph=False)
+    st = srv.run(reqs)
+    assert st["rejected"] == 1 and st["requests"] == 6
+    assert reqs[-1].status == 7 and reqs[-1].t_done < 0
+
+
+def test_plain_server_serves_in_arrival_order(fake_cuda):
+    reqs = small_requests(20)
+    srv = PlainServer(Request(0, mg.HEX, 6, 1, 0.0), device="cpu")
+    st = srv.run(reqs)
+    assert st["requests"] == 20 and st["failed"] == 0
+    done = [r.t_done for r in sorted(reqs, key=lambda r: r.arrival)]
+    assert done == sorted(done)                                # one stream: completions in order
+
+
+def test_check_deadline():
+    serve.check_deadline(10.0, 5.0, "x", now=14.9)
+    with pytest.raises(serve.ServeTimeout, match="deadline 5.0 s"):
+        serve.check_deadline(10.0, 5.0, "x", now=15.1)
+
+
+def test_batch_server_watchdog_on_a_stream_that_never_completes(fake_cuda):
+    FakeStream.hang = True
+    srv = BatchServer(budget_bytes=1 << 30, lanes=2, caps=LaneCaps(max_meshes=4), device="cpu", use_graph=False,
+                      deadline_s=0.2)
+    t = time.perf_counter()
+    with pytest.raises(serve.ServeTimeout, match="batch of"):
+        srv.run(small_requests(10))
+    assert 0.2 <= time.perf_counter() - t < 5.0
+
+
+def test_plain_server_watchdog_on_a_stream_that_never_completes(fake_cuda):
+    FakeStream.hang = True
+    srv = PlainServer(Request(0, mg.HEX, 6, 1, 0.0), device="cpu", deadline_s=0.2)
+    t = time.perf_counter()
+    with pytest.raises(serve.ServeTimeout, match="build of request 0"):
+        srv.run(small_requests(5))
+    assert 0.2 <= time.perf_counter() - t < 5.0
