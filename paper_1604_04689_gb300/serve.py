@@ -185,6 +185,7 @@ def _stats(reqs: List[Request], t_first: float, t_last: float) -> dict:
     out = {"requests": len(reqs), "elements": int(elems), "makespan_s": span,
            "req_per_s": len(reqs) / span, "melem_per_s": elems / span / 1e6,
            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+           "p999_ms": float(np.percentile(lat, 99.9) * 1e3),
            "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3),
            "failed": int(sum(1 for r in reqs if r.status != 0))}
     if build.size:  # completion minus the start of the request's build (queueing and generation excluded)
