@@ -132,27 +132,39 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = []
         try:
             with open(self.path) as f:
-                for line in f:
-                    parts = [x.strip() for x in line.split(",")]
-                    if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
-                        rows.append(parts)
+                lines = f.readlines()
             os.unlink(self.path)
         except Exception:
             return None
-        if not rows:
-            return None
-        sm = sorted(float(r[1]) for r in rows)
-        reasons = set()
-        for r in rows:
-            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
-                                 r[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(name)
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(rows[0][2]), "reasons": sorted(reasons),
-                "samples": len(rows)}
+        return parse_clock_samples(lines)
+
+
+def parse_clock_samples(lines):
+    """Summary of nvidia-smi samples of ClockSampler.FIELDS (csv, no header,
+    no units): median SM clock, the maximum SM clock, and every throttle
+    reason seen active in any sample; None without a valid sample."""
+    rows = []
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            rows.append((float(parts[1]), float(parts[2]), parts))
+        except ValueError:      # a field nvidia-smi could not read ("[N/A]") or a torn line
+            continue
+    if not rows:
+        return None
+    sm = sorted(r[0] for r in rows)
+    reasons = set()
+    for _, _, parts in rows:
+        for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                             parts[5:9]):
+            if val.lower().startswith("active"):
+                reasons.add(name)
+    return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": rows[0][1], "reasons": sorted(reasons),
+            "samples": len(rows)}
 
 
 # ---------------------------------------------------------------- baseline
