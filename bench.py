@@ -69,6 +69,8 @@ def parse():
                     help="sortpipe: the paper's sort / unique-by-key pipeline on the GPU with library primitives "
                          "(benchmark-only comparison, not part of the library)")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="tri2048")
+    ap.add_argument("--mesh-file", default="",
+                    help="build a surface mesh read from this .ply or .obj file instead of a generated workload")
     ap.add_argument("--want", choices=list(WANT), default="both")
     ap.add_argument("--no-baseline", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
@@ -99,6 +101,18 @@ def measured_peaks():
 def make_mesh(name):
     from paper_1604_04689_gb300 import meshgen
     return WORKLOADS[name][0](meshgen)
+
+
+def load_workload(args):
+    """(workload name, description, mesh) of a single-mesh run: the generated
+    workload, or the surface mesh of --mesh-file."""
+    if args.mesh_file:
+        from paper_1604_04689_gb300 import meshio
+        mesh = meshio.read_mesh(args.mesh_file)
+        base = os.path.basename(args.mesh_file)
+        return (f"file:{base}", f"surface mesh read from {base} ({mesh.n_nodes} vertices, {mesh.n_elems} faces)",
+                mesh)
+    return args.workload, WORKLOADS[args.workload][1], make_mesh(args.workload)
 
 
 # ------------------------------------------------------------------ clocks
@@ -455,7 +469,7 @@ def main():
             dist.barrier()
 
     want = WANT[args.want]
-    mesh = make_mesh(args.workload)
+    workload, description, mesh = load_workload(args)
     b = nn.Builder(dev)
     dm = nn.DeviceMesh.from_host(mesh, device=dev)
     tuning = None
@@ -533,7 +547,7 @@ def main():
         try:
             with open(tpath) as f:
                 tr = json.load(f)
-            key = f"{args.workload}:{args.want}:{KERNEL_OF_STAGE[dom]}"
+            key = f"{workload}:{args.want}:{KERNEL_OF_STAGE[dom]}"
             if key in tr and tr[key].get("source") == source_digest():
                 traffic = tr[key]["bytes_per_launch"]
         except Exception:
@@ -559,7 +573,7 @@ def main():
         "value": value, "unit": "Melem/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
-        "config": {"workload": args.workload, "description": WORKLOADS[args.workload][1],
+        "config": {"workload": workload, "description": description,
                    "want": args.want, "n_nodes": N, "n_elems": T, "nnz": nnz,
                    "l2": f"flushed before every timed step ({flush.numel() >> 20} MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU", "plan": plan,

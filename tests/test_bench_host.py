@@ -47,3 +47,17 @@ def test_source_digest_follows_only_the_measured_sources(tmp_path, monkeypatch):
     with open(copy / "nn_bucket.cu", "a") as f:
         f.write("\n")
     assert bench.source_digest() != d0
+
+
+def test_load_workload_generated_and_from_file(tmp_path, monkeypatch):
+    from paper_1604_04689_gb300 import meshgen as mg
+    from paper_1604_04689_gb300 import meshio
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "tri64"])
+    name, desc, mesh = bench.load_workload(bench.parse())
+    assert name == "tri64" and desc == bench.WORKLOADS["tri64"][1] and mesh.n_elems == 7938
+    path = tmp_path / "bunny.ply"
+    meshio.write_ply(mg.tri_grid(50, 2), str(path))
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--mesh-file", str(path)])
+    name, desc, mesh = bench.load_workload(bench.parse())
+    assert name == "file:bunny.ply" and "2500 vertices, 4802 faces" in desc
+    assert mesh.etype == mg.TRI and mesh.n_nodes == 2500
