@@ -429,3 +429,17 @@ def test_pins_catch_oracle_mutants():
             except subprocess.TimeoutExpired:   # run() has killed the child
                 rc = "hung"
             assert rc != 0, f"mutant {name} survived the pins"
+
+
+def test_non_manifold_book_and_bowtie():
+    """Hand-derived rows (Sec. 2.1.1 / 2.1.2 read as sets) for inputs a grid
+    never has.  Book: three triangles on one edge 0-1, pages 2, 3, 4.
+    Bowtie: two triangles meeting only at node 2."""
+    book = mg.from_elements([(mg.TRI, (0, 1, 2)), (mg.TRI, (1, 0, 3)), (mg.TRI, (0, 4, 1))], 5, "book")
+    r = oracle.neighbors(book)
+    assert pins.rows_of(*r["nodes"]) == [[1, 2, 3, 4], [0, 2, 3, 4], [0, 1], [0, 1], [0, 1]]
+    assert pins.rows_of(*r["elems"]) == [[0, 1, 2], [0, 1, 2], [0], [1], [2]]
+    bowtie = mg.from_elements([(mg.TRI, (0, 1, 2)), (mg.TRI, (2, 3, 4))], 5, "bowtie")
+    r = oracle.neighbors(bowtie)
+    assert pins.rows_of(*r["nodes"]) == [[1, 2], [0, 2], [0, 1, 3, 4], [2, 4], [2, 3]]
+    assert pins.rows_of(*r["elems"]) == [[0], [0], [0, 1], [1], [1]]
