@@ -477,6 +477,8 @@ class Builder:
             nbytes, _, _ = self.query(dm, want)
             ws = self.workspace(nbytes)
             ws_bytes = nbytes
+        elif ws_bytes is None:   # a caller's workspace: all of it
+            ws_bytes = ws.numel() * ws.element_size()
         s = (stream or torch.cuda.current_stream(self.device)).cuda_stream
         mesh = dm.struct()
 
