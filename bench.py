@@ -42,6 +42,10 @@ WORKLOADS = {
                "hex grid 257^3 (16,974,593 nodes, 16,777,216 hexes), seed 3, node ids permuted"),
     "mixed257": (lambda mg: mg.workload_mesh("mixed257"),
                  "hex grid 257^3 with 30% of cells split into 6 tets, seed 103"),
+    "tet101": (lambda mg: mg.tet_grid(101, 6),
+               "Kuhn tet grid 101^3 (1,030,301 nodes, 6,000,000 tets), seed 6, permuted; a profiling case"),
+    "hex129": (lambda mg: mg.hex_grid(129, 7),
+               "hex grid 129^3 (2,146,689 nodes, 2,097,152 hexes), seed 7, node ids permuted; a profiling case"),
     "tri1448": (lambda mg: mg.tri_grid(1448, 5),
                 "triangle grid 1448x1448 (2,096,704 nodes, 4,187,618 tris), seed 5, permuted "
                 "(the profiling case: records exceed L2, a few hundred MB on the device)"),

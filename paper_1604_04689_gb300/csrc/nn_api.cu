@@ -66,6 +66,7 @@ struct Plan {
     int bucket_grid = 0;
     int bucket_threads = 256;
     int wide = 0;
+    int rec_smem = 1;
     size_t bucket_smem = 0;
     uint32_t area_words = 0;
 };
@@ -104,11 +105,13 @@ nn_status make_plan_range(const nn_handle* h, const nn_mesh* m, int want, int64_
     p.k = (m->type == NN_TRI || m->type == NN_QUAD) ? 2 : 3;
 
     // bucket kernel shape.  Every node goes to one lane, which holds up to
-    // 16 (or, "wide", 32) records and a 16 (32) slot neighbour table in
-    // registers; meshes whose nodes have more than ten incidences on average
-    // (tets, mixed) take the wide form.  256-thread CTAs, two per SM.  The bucket width is then as
-    // many nodes as fit the CTA's shared memory with room to spare for nodes
-    // of higher than average valence.
+    // 16 (or, "wide", 32) records and a 16 (32) slot neighbour table;
+    // meshes whose nodes have more than ten incidences on average (tets,
+    // mixed) take the wide form.  256-thread CTAs, two per SM.  A bucket's
+    // records are copied into the CTA's shared memory beside each record's
+    // slot, its record groups, element rows and neighbour rows; the bucket
+    // width is as many nodes as fit with room to spare for buckets of higher
+    // than average record counts.
     const double inc = p.N > 0 ? (double)p.n_conn / (double)p.N : 0.0;
     p.wide = inc > 10.0 ? 1 : 0;
     const int ucap = p.wide ? 24 : 12;  // distinct neighbours a lane's table takes
@@ -118,20 +121,45 @@ nn_status make_plan_range(const nn_handle* h, const nn_mesh* m, int want, int64_
     // distinct neighbours per node: half the candidates, at most two thirds
     // of what a lane's table takes (a Kuhn tet grid has 14 for 72 candidates)
     const double U = (want & NN_WANT_NODES) ? std::min(p.k * inc / 2.0, ucap * 2.0 / 3.0) : 0.0;
-    const double per_node = 4.0 * (inc + ((want & NN_WANT_ELEMS) ? inc : 0.0) + U);  // groups, elements, neighbours
+    // record width of a bucket shift s (the fine-digit field of a two-level
+    // partition included, at most 12 bits)
+    const int eb_ = bits_for(p.T > 0 ? (uint64_t)(p.T - 1) : 0), nb_ = bits_for((uint64_t)m->n_nodes);
+    auto rb_of = [&](int s) {
+        const int bits = s + ((want & NN_WANT_ELEMS) ? 1 + eb_ : 0) + ((want & NN_WANT_NODES) ? p.k * nb_ : 0);
+        int cs_ = 0;
+        while ((((p.N + (1ll << s) - 1) >> s) + (1ll << cs_) - 1) >> cs_ > 256) ++cs_;
+        return bits + cs_ <= 64 ? 8 : 16;
+    };
+    // shared memory of a bucket of 2^s nodes with 15 % more records than
+    // average: the records themselves (when copied in), a slot and a group
+    // entry per record, element rows, neighbour rows
+    bool rec_smem = true;
+    auto bucket_bytes = [&](int s) {
+        const double n = (double)(1 << s) * 1.15;
+        return n * (inc * ((rec_smem ? rb_of(s) : 0) + 8.0) + 4.0 * (rec_smem ? std::max(U, inc) : U)) + 64.0;
+    };
     // (many buckets are fine: the histogram pass counts them in chunks that
     // fit its shared memory; the hard cap below only bounds workspace tables)
     const int64_t B_lim = (int64_t)1 << 20;
     auto fixed_of = [&](int s) { return bucket_fixed_bytes(s, p.bucket_threads, p.wide); };
-    int sb = -1;
-    for (int s = SB_MAX; s >= SB_MIN; --s) {
-        if (((p.N + (1ll << s) - 1) >> s) > B_lim) break;
-        const double area = (double)bsmem - (double)fixed_of(s);
-        if (area > 0 && (double)(1 << s) * per_node <= 0.9 * area) {
-            sb = s;
-            break;
+    auto widest = [&]() {
+        for (int s = SB_MAX; s >= SB_MIN; --s) {
+            if (((p.N + (1ll << s) - 1) >> s) > B_lim) break;
+            const double area = (double)bsmem - (double)fixed_of(s);
+            if (area > 0 && bucket_bytes(s) <= area) return s;
         }
+        return -1;
+    };
+    // records in shared memory unless that leaves a bucket fewer nodes than
+    // the CTA has lanes
+    int sb = widest();
+    if (sb >= 0 && (32 << (sb - 5)) < p.bucket_threads && sb < SB_MAX) {
+        rec_smem = false;
+        const int s2 = widest();
+        if (s2 > sb) sb = s2;
+        else rec_smem = true;
     }
+    p.rec_smem = rec_smem ? 1 : 0;
     if (sb < 0) sb = SB_MIN;
     if (h->tuning.sb >= SB_MIN && h->tuning.sb <= SB_MAX) sb = h->tuning.sb;
     if (h->sb_override >= SB_MIN && h->sb_override <= SB_MAX) sb = h->sb_override;
@@ -216,7 +244,14 @@ nn_status make_plan_range(const nn_handle* h, const nn_mesh* m, int want, int64_
     p.zero_end = o;
     p.off_spill = o;
     p.ws_min = o;
-    const size_t spill = ((size_t)16 << 20) + (size_t)p.n_conn * 8;
+    // spill area: buckets larger than the bucket pass's shared memory keep
+    // their record groups and rows there (16 MB and 8 bytes per record covers
+    // the odd oversized bucket, a node of very high valence included); a
+    // plan whose typical bucket does not fit (a tuning that widens the
+    // buckets) gets room for all of them
+    size_t spill = ((size_t)16 << 20) + (size_t)p.n_conn * 8;
+    if (bucket_bytes(sb) > (double)p.area_words * 4.0)
+        spill += (size_t)p.n_conn * (8 + 4 * (size_t)p.k) + (size_t)p.B * 64;
     p.ws_rec = o + spill;
 
     *P = p;
@@ -360,6 +395,7 @@ nn_status enqueue(nn_handle* h, const nn_mesh* m, const Plan& p, nn_csr* nodes, 
     bp.status = d_status;
     bp.area_words = p.area_words;
     bp.wide = p.wide;
+    bp.rec_smem = p.rec_smem;
     bp.ntmp = reinterpret_cast<uint32_t*>(w + p.off_ntmp);
     bp.ubk = reinterpret_cast<uint32_t*>(w + p.off_ubk);
     bp.nloc = reinterpret_cast<uint32_t*>(w + p.off_nloc);
@@ -432,11 +468,12 @@ nn_status batch_plan(const nn_handle* h, const nn_batch_caps* c, BatchPlan* out)
     p.elem_off_off = p.meshes_off + align_up((size_t)c->max_meshes * sizeof(BatchMesh));
     p.bucket_off_off = p.elem_off_off + align_up(((size_t)c->max_meshes + 1) * 8);
     p.table_bytes = p.bucket_off_off + align_up(((size_t)c->max_meshes + 1) * 8);
-    // bucket kernel: wide lanes (a batch may hold any element type), 128
-    // threads, four CTAs per SM while the bucket fits
-    p.bucket_threads = 128;
+    // bucket kernel: wide lanes (a batch may hold any element type), 256
+    // threads, two CTAs per SM, so that a bucket's records (copied into
+    // shared memory) fit beside its tables
+    p.bucket_threads = 256;
     const size_t fixed = bucket_fixed_bytes(p.sb, p.bucket_threads, 1);
-    p.bucket_smem = std::min(h->bucket_smem, h->smem_per_sm / 4 - 2048);
+    p.bucket_smem = std::min(h->bucket_smem, h->smem_per_sm / 2 - 2048);
     if (fixed + 8192 * 4 > p.bucket_smem) p.bucket_smem = h->bucket_smem;
     if (fixed + 4096 * 4 > p.bucket_smem) return NN_ERR_ARG;
     p.area_words = (uint32_t)((p.bucket_smem - fixed) / 4);
@@ -598,6 +635,7 @@ nn_status batch_launch(nn_handle* h, const nn_batch_caps* c, const void* staging
     kp.fmt.rb = 16;
     kp.fmt.k = 3;
     kp.wide = 1;
+    kp.rec_smem = 1;
     kp.ntmp = reinterpret_cast<uint32_t*>(w + bp.off_ntmp);
     kp.ubk = reinterpret_cast<uint32_t*>(w + bp.off_ubk);
     kp.nloc = reinterpret_cast<uint32_t*>(w + bp.off_nloc);

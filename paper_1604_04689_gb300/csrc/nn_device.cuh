@@ -155,12 +155,16 @@ __device__ __forceinline__ void rec_put(Rec& r, uint64_t val, int off) {  // val
         r.hi |= val << (off - 64);
     }
 }
-__device__ __forceinline__ uint32_t rec_get(const Rec& r, int off, int width) {  // width <= 32
-    uint64_t v;
-    if (off >= 64) v = r.hi >> (off - 64);
-    else if (off == 0) v = r.lo;
-    else v = (r.lo >> off) | (r.hi << (64 - off));
-    return (uint32_t)(v & ((1ull << width) - 1));
+// Field of `width` <= 32 bits at bit `off` of the 128-bit record (no field
+// crosses bit 128).  Branch-free: the field starts in 32-bit word off / 32
+// and a funnel shift takes it across into the next word.
+__device__ __forceinline__ uint32_t rec_get(const Rec& r, int off, int width) {
+    const uint32_t w0 = (uint32_t)r.lo, w1 = (uint32_t)(r.lo >> 32), w2 = (uint32_t)r.hi, w3 = (uint32_t)(r.hi >> 32);
+    const int q = off >> 5;
+    const uint32_t a = q == 0 ? w0 : (q == 1 ? w1 : (q == 2 ? w2 : w3));
+    const uint32_t b = q == 0 ? w1 : (q == 1 ? w2 : (q == 2 ? w3 : 0u));
+    const uint32_t v = __funnelshift_r(a, b, (uint32_t)off & 31u);
+    return width >= 32 ? v : v & ((1u << width) - 1u);
 }
 
 // ------------------------------------------------ element local edge tables

@@ -134,6 +134,7 @@ struct BucketParams {
     uint32_t* ubk;          // [n_buckets] node-row total of each bucket
     uint32_t* nloc;         // [n_buckets << sb] each node's offset within its bucket's rows
     int32_t wide;           // 1: 32 records and a 32-slot table per node in registers, 0: 16 and 16
+    int32_t rec_smem;       // 1: copy each bucket's records into shared memory when they fit, 0: read them from L2
     BatchTables batch;      // batch.hdr != nullptr: format, bucket count and meshes come from the tables
     const int32_t* batch_err;  // batches: status of the shared offsets scan, copied to every mesh
     const int64_t* base;    // chunked builds: {element-CSR, node-CSR} entries of the earlier chunks (else nullptr)
