@@ -4,13 +4,19 @@
 One step = one full build of BOTH results (neighbor-node CSR and
 neighbor-element CSR) for one seeded synthetic mesh, through the C ABI, with
 the connectivity already resident in HBM.  Metric: Melem/s (mesh elements
-processed per second, whole job).  Default workload: the 2048 x 2048
-triangle grid (4,194,304 nodes, 8,380,418 triangles, node ids and element
-order permuted).
+processed per second, whole job).  Default workload: the hex grid 257^3
+(16,974,593 nodes, 16,777,216 hexes, node ids permuted), the largest
+single-GPU configuration; the triangle grid 2048^2, the Kuhn tet grid 161^3
+and the mixed hex/tet variant of the hex grid are timed in the same run under
+"per_config", and a bounded serving run (batched vs one build per mesh)
+under "serving".
 
-Prints ONE JSON line (rank 0), with the roofline of the dominant kernel: its
-algorithmic bytes per launch (records read, CSRs written) over its CUDA-event
-time, against the measured copy bandwidth.
+Prints ONE JSON line (rank 0).  "roofline": the compulsory bytes of one build
+(read the connectivity once, write both CSRs once) over the CUDA-event time
+of the dominant kernel, against the measured copy bandwidth; the kernel's own
+implementation bytes and its ncu DRAM bytes (when a capture of the current
+source exists) are reported beside it under their own names.  "pipeline":
+the same compulsory bytes over the whole step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
 
@@ -60,8 +66,8 @@ WORKLOADS = {
 # serving workload, batched p50/p99 latency beside one build per mesh
 METRIC = "neighbor-CSR build Melem/s and % of HBM roofline; batched p50/p99 vs plain"
 WANT = {"both": 3, "nodes": 1, "elems": 2}
-KERNEL_OF_STAGE = {"hist": "k_hist", "offsets": "k_offsets", "part": "k_part", "bucket": "k_bucket",
-                   "place": "k_node_scan+k_node_copy"}
+KERNEL_OF_STAGE = {"hist": "k_hist", "offsets": "k_offsets", "part": "k_part_coarse", "part_fine": "k_part_fine",
+                   "bucket": "k_bucket", "place": "k_node_scan+k_node_copy"}
 
 
 def parse():
@@ -72,7 +78,11 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference", "sortpipe"], default="ours",
                     help="sortpipe: the paper's sort / unique-by-key pipeline on the GPU with library primitives "
                          "(benchmark-only comparison, not part of the library)")
-    ap.add_argument("--workload", choices=list(WORKLOADS), default="tri2048")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="hex257")
+    ap.add_argument("--configs", default="tri2048,tet161,mixed257",
+                    help="further workloads timed in the same run (per_config); empty: none")
+    ap.add_argument("--no-serving", action="store_true", help="skip the bounded serving run of the default line")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="requests per load of the bounded serving run")
     ap.add_argument("--mesh-file", default="",
                     help="build a surface mesh read from this .ply or .obj file instead of a generated workload")
     ap.add_argument("--want", choices=list(WANT), default="both")
@@ -187,19 +197,63 @@ def parse_clock_samples(lines):
 
 # ---------------------------------------------------------------- baseline
 
-def oracle_baseline(seconds_hint=20.0):
-    """The CPU oracle, as it stands, on a bounded sample of the same kind of mesh."""
-    import oracle
+def oracle_sample(workload):
+    """A bounded sample of the same kind of mesh as `workload` for the CPU
+    oracle: (mesh, description, elements of the sample / elements of the
+    workload)."""
     from paper_1604_04689_gb300 import meshgen
-    n = 1024
-    mesh = meshgen.tri_grid(n, 1)
-    t0 = time.perf_counter()
-    r = oracle.neighbors(mesh, oracle.BOTH)
-    dt = time.perf_counter() - t0
-    assert r["status"] == 0
+    full = {"hex257": 16777216, "mixed257": 41924166, "tet161": 24576000, "tri2048": 8380418}.get(workload)
+    if workload in ("hex257", "hex129"):
+        n, mesh = 101, meshgen.hex_grid(101, 3)
+        desc = f"hex grid {n}^3 ({mesh.n_elems} hexes, seed 3, node ids permuted)"
+    elif workload == "mixed257":
+        n, mesh = 65, meshgen.mixed_grid(65, 103)
+        desc = f"hex grid {n}^3 with 30% of cells split into 6 tets ({mesh.n_elems} elements, seed 103)"
+    elif workload in ("tet161", "tet101"):
+        n, mesh = 51, meshgen.tet_grid(51, 2)
+        desc = f"Kuhn tet grid {n}^3 ({mesh.n_elems} tets, seed 2, permuted)"
+    else:
+        n, mesh = 1024, meshgen.tri_grid(1024, 1)
+        desc = f"triangle grid {n}x{n} ({mesh.n_elems} tris, seed 1, permuted)"
+    return mesh, desc, (mesh.n_elems / full if full else None)
+
+
+def pinned_core():
+    """The host core the oracle is pinned to (the last one this process may use)."""
+    try:
+        return max(os.sched_getaffinity(0))
+    except Exception:
+        return None
+
+
+def oracle_baseline(workload, runs=3):
+    """The CPU oracle, as it stands, on a bounded sample of the same kind of
+    mesh as the workload: median of `runs` builds, this process pinned to one
+    host core meanwhile."""
+    import oracle
+    mesh, desc, ratio = oracle_sample(workload)
+    core = pinned_core()
+    old = None
+    try:
+        if core is not None:
+            old = os.sched_getaffinity(0)
+            os.sched_setaffinity(0, {core})
+        times = []
+        for _ in range(runs):
+            t0 = time.perf_counter()
+            r = oracle.neighbors(mesh, oracle.BOTH)
+            times.append(time.perf_counter() - t0)
+            assert r["status"] == 0
+    finally:
+        if old is not None:
+            os.sched_setaffinity(0, old)
+    dt = sorted(times)[len(times) // 2]
     return {"value": mesh.n_elems / dt / 1e6, "unit": "Melem/s", "cores": 1, "kind": "oracle", "host": host_info(),
-            "sample": f"triangle grid {n}x{n} ({mesh.n_elems} tris, seed 1, permuted), both CSRs, "
-                      f"single-threaded std::set oracle, {dt:.1f} s"}
+            "runs": runs, "core": core, "seconds": times,
+            "sample": f"{desc}, both CSRs, single-threaded std::set oracle, median of {runs} runs pinned to host "
+                      f"core {core}; the sample has {ratio:.4f} of the workload's elements" if ratio else
+                      f"{desc}, both CSRs, single-threaded std::set oracle, median of {runs} runs pinned to host "
+                      f"core {core}"}
 
 
 def host_info():
@@ -217,14 +271,29 @@ def host_info():
 
 
 def reference_arm(args):
-    """--impl reference: the CPU oracle timed on a bounded sample per step."""
+    """--impl reference: the CPU oracle, as it stands, timed on a bounded
+    sample of the same kind of mesh as the workload per step, pinned to one
+    host core; rank 0 alone runs it."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     from paper_1604_04689_gb300 import meshgen
-    n = 256
-    mesh = meshgen.tri_grid(n, 1)
+    if args.workload in ("hex257", "hex129", "mixed257"):
+        n = 41
+        mesh = meshgen.hex_grid(n, 3) if args.workload != "mixed257" else meshgen.mixed_grid(n, 103)
+        sample = f"{'hex' if args.workload != 'mixed257' else 'mixed hex/tet'} grid {n}^3 ({mesh.n_elems} elements)"
+    elif args.workload in ("tet161", "tet101"):
+        n = 31
+        mesh = meshgen.tet_grid(n, 2)
+        sample = f"Kuhn tet grid {n}^3 ({mesh.n_elems} tets)"
+    else:
+        n = 256
+        mesh = meshgen.tri_grid(n, 1)
+        sample = f"triangle grid {n}x{n} ({mesh.n_elems} tris)"
+    core = pinned_core()
+    if core is not None:
+        os.sched_setaffinity(0, {core})
     for _ in range(args.warmup):
         oracle.neighbors(mesh, WANT[args.want])
     t0 = time.perf_counter()
@@ -233,8 +302,8 @@ def reference_arm(args):
         assert r["status"] == 0
     dt = time.perf_counter() - t0
     v = mesh.n_elems * args.steps / dt / 1e6
-    sample = (f"triangle grid {n}x{n} ({mesh.n_elems} tris, seed 1, permuted) per step, single-threaded "
-              f"std::set oracle on the host")
+    sample = (f"{sample} per step, seeded and permuted like the workload, single-threaded std::set oracle on the "
+              f"host, pinned to core {core}")
     line = {"metric": METRIC, "value": v, "unit": "Melem/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
@@ -474,6 +543,59 @@ def main():
 
     want = WANT[args.want]
     workload, description, mesh = load_workload(args)
+    head = time_build(torch, nn, dev, workload, description, mesh, args, want, world, barrier,
+                      clocks=not args.no_clocks, e2e=not args.no_e2e, elem_adj=args.elem_adj)
+    del mesh
+
+    # further configurations in the same run (single GPU only: their timed
+    # regions are their own, after the headline's)
+    per_config = {}
+    if world == 1 and not args.mesh_file:
+        for name in [x.strip() for x in args.configs.split(",") if x.strip() and x.strip() != workload]:
+            m = make_mesh(name)
+            r = time_build(torch, nn, dev, name, WORKLOADS[name][1], m, args, want, world, barrier)
+            per_config[name] = {k: r[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup", "config",
+                                                  "roofline", "pipeline", "gpu_launches")}
+            del m
+            torch.cuda.empty_cache()
+
+    serving = None
+    if world == 1 and not args.no_serving:
+        torch.cuda.empty_cache()
+        serving = serving_summary(args)
+
+    baseline = None
+    if rank == 0 and world == 1 and not args.no_baseline:
+        baseline = oracle_baseline(workload)
+
+    line = {
+        "metric": METRIC,
+        "value": head["value"], "unit": "Melem/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": head["config"],
+        "roofline": head["roofline"],
+        "pipeline": head["pipeline"],
+        "gpu_launches": head["gpu_launches"],
+        "clocks": head["clocks"],
+        "e2e": head["e2e"],
+        "cpu_baseline": baseline,
+        "per_config": per_config,
+        "serving": serving,
+    }
+    if head.get("element_adjacency") is not None:
+        line["element_adjacency"] = head["element_adjacency"]
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def time_build(torch, nn, dev, workload, description, mesh, args, want, world, barrier, clocks=False, e2e=False,
+               elem_adj=False):
+    """Time `args.steps` builds of `mesh` (after `args.warmup` untimed ones,
+    L2 flushed before each, CUDA events on the launching stream, barriers and
+    the maximum over ranks around the timed region) and account its bytes."""
     b = nn.Builder(dev)
     dm = nn.DeviceMesh.from_host(mesh, device=dev)
     tuning = None
@@ -498,8 +620,8 @@ def main():
     assert int(b.status.item()) == 0, nn.STATUS[int(b.status.item())]
 
     # ---- timed region: K builds, L2 flushed before each (outside the events)
-    sampler = ClockSampler(local)
-    if not args.no_clocks:
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    if clocks:
         sampler.start()
         time.sleep(0.3)
     nn.nn_profile_enable(b.h, True)
@@ -519,90 +641,119 @@ def main():
     t_wall = time.perf_counter() - t_wall
     stage_ms, calls = nn.nn_profile_read(b.h)
     nn.nn_profile_enable(b.h, False)
-    clocks = None if args.no_clocks else sampler.stop()
+    clk = sampler.stop() if clocks else None
     status = int(b.status.item())
     assert status == 0, nn.STATUS[status]
     per_step = sorted(s.elapsed_time(e) for s, e in zip(starts, ends))
-    total_ms = sum(per_step)
-    total_ms = max_over_ranks(total_ms, world, dev)
+    total_ms = max_over_ranks(sum(per_step), world, dev)
 
-    # ---- result sizes and algorithmic bytes
-    nnz = {}
-    for k, (rp, col) in out.items():
-        nnz[k] = int(rp[-1].item())
+    # ---- result sizes and bytes
+    nnz = {k: int(rp[-1].item()) for k, (rp, col) in out.items()}
     N, T, n_conn = mesh.n_nodes, mesh.n_elems, mesh.n_conn
+    ms_per_step = total_ms / args.steps
+    stage = {k: v / max(calls, 1) for k, v in stage_ms.items()}
+    acc = roofline_accounting(plan, N, T, n_conn, nnz, stage, workload, args.want)
+    value = whole_job_value(T, args.steps, world, total_ms)
+    pipeline = {"alg_bytes_per_step": acc["compulsory"],
+                "achieved_gbs": acc["compulsory"] / (ms_per_step * 1e-3) / 1e9,
+                "frac": acc["compulsory"] / (ms_per_step * 1e-3) / 1e9 / acc["peak"],
+                "stage_ms_per_step": stage,
+                "step_ms_median": per_step[len(per_step) // 2],
+                "step_ms_p95": per_step[min(len(per_step) - 1, int(0.95 * len(per_step)))],
+                "wall_s": t_wall}
+
+    r = {"value": value, "unit": "Melem/s", "ms_per_step": ms_per_step, "steps": args.steps, "warmup": args.warmup,
+         "config": {"workload": workload, "description": description,
+                    "want": args.want, "n_nodes": N, "n_elems": T, "nnz": nnz,
+                    "l2": f"flushed before every timed step ({flush.numel() >> 20} MiB write)",
+                    "parallelism": "replicas" if world > 1 else "single GPU", "plan": plan,
+                    "tuning": tuning},
+         "roofline": acc["roofline"], "pipeline": pipeline,
+         "gpu_launches": launches_per_build(plan, args.want) * args.steps, "clocks": clk, "e2e": None}
+    if e2e:
+        r["e2e"] = end_to_end(torch, nn, b, mesh, dm, want, ws, ws_bytes, out, args.steps, dev, world)
+    if elem_adj and "elems" in out:
+        r["element_adjacency"] = time_adjacency(torch, nn, b, dm, out, flush, stream, max(args.steps // 2, 3))
+    del ws, out, flush, dm
+    return r
+
+
+def roofline_accounting(plan, N, T, n_conn, nnz, stage, workload, want):
+    """Roofline of the dominant kernel.  frac: the compulsory bytes of one
+    build -- the connectivity read once, each CSR (row pointers and columns)
+    written once -- over the dominant kernel's CUDA-event time per launch,
+    against the measured copy bandwidth.  Beside it, under their own names:
+    the kernel's own implementation bytes per launch (records it reads,
+    tables, rows it writes) and, when a capture of the current source
+    exists, its ncu DRAM bytes per launch."""
     rb, G, B = plan["record_bytes"], plan["emit_ctas"], plan["n_buckets"]
     out_bytes = sum(8 * (N + 1) + 4 * v for v in nnz.values())
-    alg = {  # compulsory bytes each stage must move, per launch
+    compulsory = 4 * n_conn + out_bytes
+    two_level = plan["partition"] > 0
+    own = {  # bytes each kernel moves by its design, per launch
         "hist": 4 * n_conn + 4 * G * B,
         "offsets": 3 * 4 * G * B + 4 * (B + 1),
-        "part": 4 * n_conn + 4 * G * B + rb * n_conn,
+        "part": 4 * n_conn + rb * n_conn,
+        "part_fine": 2 * rb * n_conn if two_level else 0,
         "bucket": rb * n_conn + 4 * (B + 1) + out_bytes,
-        "place": (8 * (N + 1) + 4 * nnz["nodes"]) if "nodes" in nnz else 0,
+        "place": 2 * (8 * (N + 1) + 4 * nnz["nodes"]) if "nodes" in nnz else 0,
     }
-    pipeline_bytes = 4 * n_conn + out_bytes      # read connectivity once, write the CSRs once
     peak, peak_src = measured_peaks()
-    dom = max(alg, key=lambda k: stage_ms.get(k, 0.0))
-    dom_ms = stage_ms[dom] / max(calls, 1)
-    achieved = alg[dom] / (dom_ms * 1e-3) / 1e9
+    kernels = {k: v for k, v in stage.items() if k in KERNEL_OF_STAGE}
+    dom = max(kernels, key=kernels.get)
+    dom_ms = kernels[dom]
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
         try:
             with open(tpath) as f:
                 tr = json.load(f)
-            key = f"{workload}:{args.want}:{KERNEL_OF_STAGE[dom]}"
+            key = f"{workload}:{want}:{KERNEL_OF_STAGE[dom]}"
             if key in tr and tr[key].get("source") == source_digest():
                 traffic = tr[key]["bytes_per_launch"]
         except Exception:
             traffic = None
-    ms_per_step = total_ms / args.steps
-    value = whole_job_value(T, args.steps, world, total_ms)
+    gbs = lambda nbytes: nbytes / (dom_ms * 1e-3) / 1e9
+    kernel = KERNEL_OF_STAGE[dom] if (dom != "part" or two_level) else "k_part"
+    roof = {"bound": "hbm", "kernel": kernel, "achieved": gbs(compulsory), "peak": peak,
+            "peak_source": f"{peak_src} copy bandwidth", "unit": "GB/s", "frac": gbs(compulsory) / peak,
+            "traffic": traffic, "alg_bytes_per_launch": compulsory, "ms_per_launch": dom_ms,
+            "alg_bytes": "compulsory bytes of one build: 4 n_conn + sum over CSRs of (8 (N+1) + 4 nnz)",
+            "kernel_own_bytes_per_launch": own[dom],
+            "kernel_own_bytes_frac": gbs(own[dom]) / peak,
+            "ncu_dram_frac": (gbs(traffic) / peak) if traffic else None}
+    return {"compulsory": compulsory, "peak": peak, "roofline": roof}
 
-    # ---- end to end through the public API with host buffers
-    e2e = None
-    if not args.no_e2e:
-        e2e = end_to_end(torch, nn, b, mesh, dm, want, ws, ws_bytes, out, args.steps, dev, world)
 
-    adjacency = None
-    if args.elem_adj and "elems" in out:
-        adjacency = time_adjacency(torch, nn, b, dm, out, flush, stream, max(args.steps // 2, 3))
-
-    baseline = None
-    if rank == 0 and world == 1 and not args.no_baseline:
-        baseline = oracle_baseline()
-
-    line = {
-        "metric": METRIC,
-        "value": value, "unit": "Melem/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "int32", "data": "synthetic",
-        "config": {"workload": workload, "description": description,
-                   "want": args.want, "n_nodes": N, "n_elems": T, "nnz": nnz,
-                   "l2": f"flushed before every timed step ({flush.numel() >> 20} MiB write)",
-                   "parallelism": "replicas" if world > 1 else "single GPU", "plan": plan,
-                   "tuning": tuning},
-        "roofline": {"bound": "hbm", "kernel": KERNEL_OF_STAGE[dom], "achieved": achieved, "peak": peak,
-                     "peak_source": f"{peak_src} copy bandwidth", "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "alg_bytes_per_launch": alg[dom], "ms_per_launch": dom_ms},
-        "pipeline": {"alg_bytes_per_step": pipeline_bytes,
-                     "achieved_gbs": pipeline_bytes / (ms_per_step * 1e-3) / 1e9,
-                     "frac": pipeline_bytes / (ms_per_step * 1e-3) / 1e9 / peak,
-                     "stage_ms_per_step": {k: v / max(calls, 1) for k, v in stage_ms.items()},
-                     "step_ms_median": per_step[len(per_step) // 2],
-                     "step_ms_p95": per_step[min(len(per_step) - 1, int(0.95 * len(per_step)))],
-                     "wall_s": t_wall},
-        "gpu_launches": launches_per_build(plan, args.want) * args.steps,
-        "clocks": clocks,
-        "e2e": e2e,
-        "cpu_baseline": baseline,
-    }
-    if adjacency is not None:
-        line["element_adjacency"] = adjacency
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+def serving_summary(args):
+    """A bounded serving run for the default line: the plain server's
+    saturated rate R, then the same Poisson trace at 0.8 R and 1.5 R served by
+    one build per mesh (plain) and by continuous batching over two lanes;
+    throughput and latency percentiles of each."""
+    import copy
+    from paper_1604_04689_gb300.serve import BatchServer, PlainServer, make_requests
+    n = max(args.serve_requests, 100)
+    base = make_requests(n, 0.0)
+    big = max(base, key=lambda r: r.n_conn)
+    plain = PlainServer(big)
+    batched = BatchServer(budget_bytes=40 << 30, lanes=2)
+    w = min(200, n)
+    plain.run(copy.deepcopy(base[:w]))
+    batched.run(copy.deepcopy(base[:w]))
+    sat = plain.run(copy.deepcopy(base))
+    keys = ("req_per_s", "melem_per_s", "p50_ms", "p99_ms", "p999_ms", "build_p99_ms", "failed")
+    loads = {}
+    for ld in (0.8, 1.5):
+        tr = make_requests(n, ld * sat["req_per_s"])
+        rp = plain.run(copy.deepcopy(tr))
+        rb = batched.run(copy.deepcopy(tr))
+        loads[str(ld)] = {"rate_req_per_s": ld * sat["req_per_s"],
+                          "plain": {k: rp.get(k) for k in keys}, "batched": {k: rb.get(k) for k in keys}}
+    del plain, batched
+    return {"requests": n, "plain_saturated_req_per_s": sat["req_per_s"], "budget_bytes": 40 << 30, "lanes": 2,
+            "description": "tri / Kuhn tet / hex grid requests (1e3-2e6 elements, log-uniform, seeded), "
+                           "connectivity generated on the device per request; latency = completion - arrival",
+            "loads": loads}
 
 
 def end_to_end(torch, nn, b, mesh, dm, want, ws, ws_bytes, out, steps, dev, world):

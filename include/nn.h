@@ -292,13 +292,14 @@ nn_status nn_generate_grid(int32_t type, int64_t n, uint64_t seed, int permute_n
 /* Per-stage device timing (used by the benchmark).  While enabled, compute
  * calls record CUDA events on their stream between their stages:
  *   0 workspace/status init, 1 bucket histogram, 2 bucket offsets,
- *   3 partition (record write), 4 bucket pass (element CSR, node rows to
- *   scratch), 5 node-row placement.
+ *   3 partition (record write; the coarse pass of a two-level partition),
+ *   4 fine partition pass (empty for a one-level partition), 5 bucket pass
+ *   (element CSR, node rows to scratch), 6 node-row placement.
  * nn_profile_read waits for the recorded events and returns, per stage, the
  * summed milliseconds over the calls since profiling was enabled, and the
  * number of calls.  n_stages <= NN_PROFILE_STAGES.  Enabling twice resets the
  * sums.  Chunked builds and batches record no stages. */
-#define NN_PROFILE_STAGES 6
+#define NN_PROFILE_STAGES 7
 nn_status nn_profile_enable(nn_handle* h, int enable);
 nn_status nn_profile_read(nn_handle* h, double* ms, int64_t* calls, int n_stages);
 

@@ -406,14 +406,17 @@ nn_status enqueue(nn_handle* h, const nn_mesh* m, const Plan& p, nn_csr* nodes, 
     if (launch_offsets(op, s) != cudaSuccess) return NN_ERR_CUDA;
     mark(3);
     if (p.fmt.cshift >= 0) {
-        if (launch_part_sorted(ep, op.bstart, p.G_fine, s) != cudaSuccess) return NN_ERR_CUDA;
-    } else if (launch_part(ep, s) != cudaSuccess) {
-        return NN_ERR_CUDA;
+        if (launch_part_coarse(ep, s) != cudaSuccess) return NN_ERR_CUDA;
+        mark(4);
+        if (launch_part_fine(ep, op.bstart, p.G_fine, s) != cudaSuccess) return NN_ERR_CUDA;
+    } else {
+        if (launch_part(ep, s) != cudaSuccess) return NN_ERR_CUDA;
+        mark(4);
     }
-    mark(4);
+    mark(5);
     if (launch_bucket(bp, p.bucket_grid, p.bucket_threads, p.bucket_smem, s) != cudaSuccess)
         return NN_ERR_CUDA;
-    mark(5);
+    mark(6);
     if (want & NN_WANT_NODES) {
         CompactParams cp{};
         cp.n_buckets = p.B;
@@ -436,7 +439,7 @@ nn_status enqueue(nn_handle* h, const nn_mesh* m, const Plan& p, nn_csr* nodes, 
         if (launch_node_compact(cp, (int)std::min<int64_t>(p.B, (int64_t)h->sms * 8), s) != cudaSuccess)
             return NN_ERR_CUDA;
     }
-    mark(6);
+    mark(7);
     return NN_OK;
 }
 

@@ -676,11 +676,24 @@ void coarse_r(const EmitParams& p, cudaStream_t s) {
 }
 
 template <int TYPE>
-cudaError_t part_sorted_t(const EmitParams& p, const uint32_t* bstart, int grid_fine, cudaStream_t s) {
+cudaError_t part_coarse_t(const EmitParams& p, cudaStream_t s) {
     if (ranged(p)) coarse_r<TYPE, true>(p, s);
     else coarse_r<TYPE, false>(p, s);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || p.fmt.cshift <= 0) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_part_coarse(const EmitParams& p, cudaStream_t s) {
+    switch (p.type) {
+        case NN_TRI: return part_coarse_t<NN_TRI>(p, s);
+        case NN_QUAD: return part_coarse_t<NN_QUAD>(p, s);
+        case NN_TET: return part_coarse_t<NN_TET>(p, s);
+        case NN_HEX: return part_coarse_t<NN_HEX>(p, s);
+        default: return part_coarse_t<NN_MIXED>(p, s);
+    }
+}
+
+cudaError_t launch_part_fine(const EmitParams& p, const uint32_t* bstart, int grid_fine, cudaStream_t s) {
+    if (p.fmt.cshift <= 0) return cudaSuccess;
     const size_t fs = fine_smem(1 << p.fmt.cshift);
     if (p.fmt.rb == 8) k_part_fine<8><<<grid_fine, SORT_THREADS, fs, s>>>(p, bstart);
     else k_part_fine<16><<<grid_fine, SORT_THREADS, fs, s>>>(p, bstart);
@@ -688,13 +701,9 @@ cudaError_t part_sorted_t(const EmitParams& p, const uint32_t* bstart, int grid_
 }
 
 cudaError_t launch_part_sorted(const EmitParams& p, const uint32_t* bstart, int grid_fine, cudaStream_t s) {
-    switch (p.type) {
-        case NN_TRI: return part_sorted_t<NN_TRI>(p, bstart, grid_fine, s);
-        case NN_QUAD: return part_sorted_t<NN_QUAD>(p, bstart, grid_fine, s);
-        case NN_TET: return part_sorted_t<NN_TET>(p, bstart, grid_fine, s);
-        case NN_HEX: return part_sorted_t<NN_HEX>(p, bstart, grid_fine, s);
-        default: return part_sorted_t<NN_MIXED>(p, bstart, grid_fine, s);
-    }
+    cudaError_t e = launch_part_coarse(p, s);
+    if (e != cudaSuccess) return e;
+    return launch_part_fine(p, bstart, grid_fine, s);
 }
 
 template <int TYPE>

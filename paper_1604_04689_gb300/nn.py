@@ -359,7 +359,7 @@ def generate_grid(etype: int, n: int, seed: int, permute_nodes: bool = True, per
     return DeviceMesh(etype, N, conn)
 
 
-STAGES = ("init", "hist", "offsets", "part", "bucket", "place")
+STAGES = ("init", "hist", "offsets", "part", "part_fine", "bucket", "place")
 
 
 def nn_profile_enable(h: int, enable: bool) -> None:

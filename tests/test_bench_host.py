@@ -61,3 +61,31 @@ def test_load_workload_generated_and_from_file(tmp_path, monkeypatch):
     name, desc, mesh = bench.load_workload(bench.parse())
     assert name == "file:bunny.ply" and "2500 vertices, 4802 faces" in desc
     assert mesh.etype == mg.TRI and mesh.n_nodes == 2500
+
+
+def test_roofline_is_the_compulsory_bytes_over_the_dominant_kernel():
+    plan = {"record_bytes": 16, "emit_ctas": 152, "n_buckets": 66308, "partition": 9}
+    N, T, n_conn = 16_974_593, 16_777_216, 134_217_728
+    nnz = {"nodes": 101_451_264, "elems": 134_217_728}
+    stage = {"init": 0.01, "hist": 0.3, "offsets": 0.03, "part": 1.0, "part_fine": 1.4, "bucket": 2.4, "place": 0.2}
+    acc = bench.roofline_accounting(plan, N, T, n_conn, nnz, stage, "hex257", "both")
+    compulsory = 4 * n_conn + 2 * 8 * (N + 1) + 4 * (nnz["nodes"] + nnz["elems"])
+    assert acc["compulsory"] == compulsory == 1_751_140_384  # 1751.1 MB: read conn once, write both CSRs once
+    r = acc["roofline"]
+    assert r["kernel"] == "k_bucket" and r["ms_per_launch"] == 2.4  # the slowest kernel stage ("init" is no kernel)
+    assert abs(r["achieved"] - compulsory / 2.4e-3 / 1e9) < 1e-6
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert r["alg_bytes_per_launch"] == compulsory
+    own = 16 * n_conn + 4 * (66308 + 1) + compulsory - 4 * n_conn
+    assert r["kernel_own_bytes_per_launch"] == own
+    # the fine partition as the slowest stage is named for its own kernel
+    stage["part_fine"] = 3.0
+    assert bench.roofline_accounting(plan, N, T, n_conn, nnz, stage, "hex257", "both")["roofline"]["kernel"] == \
+        "k_part_fine"
+
+
+def test_oracle_samples_match_the_workload_kind():
+    mesh, desc, ratio = bench.oracle_sample("hex257")
+    assert mesh.etype == 3 and "hex grid 101^3" in desc and abs(ratio - 100 ** 3 / 256 ** 3) < 1e-12
+    mesh, desc, ratio = bench.oracle_sample("tri2048")
+    assert mesh.etype == 0 and abs(ratio - mesh.n_elems / 8_380_418) < 1e-12

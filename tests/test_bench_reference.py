@@ -27,7 +27,8 @@ def test_reference_line_has_the_contract_keys():
         assert k in d, k
     assert d["impl"] == "reference" and d["unit"] == "Melem/s" and d["higher_is_better"] is True
     assert d["steps"] == 2 and d["warmup"] == 1 and d["value"] > 0
-    assert d["config"]["workload"] == "tri2048"
+    assert d["config"]["workload"] == "hex257"  # the default line's workload; the sample is a small hex grid
+    assert "hex grid 41^3" in d["config"]["sample"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
     e2e = d["e2e"]
