@@ -476,7 +476,8 @@ def serve_bench(args):
     big = max(base, key=lambda r: r.n_conn)
     plain = PlainServer(big)
     batched = BatchServer(budget_bytes=budget, lanes=2)
-    # warm-up: both servers on a short saturated prefix (captures the lanes' graphs)
+    # warm-up: every lane graph captured, then both servers on a short saturated prefix
+    batched.warm(min(base, key=lambda r: r.n_conn))
     w = max(args.warmup, 1) * 20
     plain.run(copy.deepcopy(base[:w]))
     batched.run(copy.deepcopy(base[:w]))
@@ -738,6 +739,7 @@ def serving_summary(args):
     plain = PlainServer(big)
     batched = BatchServer(budget_bytes=40 << 30, lanes=2)
     w = min(200, n)
+    batched.warm(min(base, key=lambda r: r.n_conn))
     plain.run(copy.deepcopy(base[:w]))
     batched.run(copy.deepcopy(base[:w]))
     sat = plain.run(copy.deepcopy(base))

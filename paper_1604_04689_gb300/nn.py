@@ -477,7 +477,9 @@ class Builder:
             nbytes, _, _ = self.query(dm, want)
             ws = self.workspace(nbytes)
             ws_bytes = nbytes
-        elif ws_bytes is None:   # a caller's workspace: all of it
+        elif ws_bytes is None:   # a caller's workspace: all of it (one contiguous span from data_ptr())
+            if not ws.is_contiguous():
+                raise ValueError("a workspace given without ws_bytes must be contiguous")
             ws_bytes = ws.numel() * ws.element_size()
         s = (stream or torch.cuda.current_stream(self.device)).cuda_stream
         mesh = dm.struct()

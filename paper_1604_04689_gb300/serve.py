@@ -1,15 +1,18 @@
 """Serving loop: continuous batching of neighbour-CSR build requests.
 
 Requests (a seeded grid mesh: type, grid side, seed) arrive over time.  The
-batched server keeps ``lanes`` independent lanes (a CUDA stream, a batch
-workspace with fixed capacity, pinned staging and a CUDA graph captured once
-around the batched launch).  Whenever a lane is free it admits the requests
-that have arrived, in arrival order, while they fit the lane's capacity and
-the device-memory budget, materialises their connectivity on the lane's stream
-(device generator, the stand-in for an upload), prepares the batch tables and
-replays the lane's graph.  While one lane's batch runs on the GPU, the next
-batch is admitted and launched on another lane, so work overlaps on the device
-and requests are admitted as lanes and memory free up.  The plain server
+batched server keeps ``lanes`` independent lanes (a CUDA stream, batch
+workspaces of a small and of the full capacity, pinned staging and a CUDA
+graph captured once around each batched launch, and a single-mesh builder).
+Whenever a lane is free it admits the requests that have arrived, in arrival
+order, while they fit the lane's capacity and the device-memory budget,
+materialises their connectivity on the lane's stream (device generator, the
+stand-in for an upload), and either builds a lone request at once with the
+single-mesh builder or prepares the batch tables and replays the graph of the
+smallest capacity that holds the batch.  While one lane's batch runs on the
+GPU, the next batch is admitted and launched on another lane, so work
+overlaps on the device and requests are admitted as lanes and memory free
+up.  The plain server
 answers the same requests one build call per mesh on one stream.
 
 Latency of a request = completion (CUDA event at the end of its batch, mapped
@@ -79,6 +82,22 @@ class LaneCaps:
     max_nodes: int = 24_000_000
     max_conn: int = 64_000_000
 
+    def holds_caps(self, other: "LaneCaps") -> bool:
+        """True when this class is no larger than `other` in every capacity."""
+        return (self.max_meshes <= other.max_meshes and self.max_elems <= other.max_elems
+                and self.max_nodes <= other.max_nodes and self.max_conn <= other.max_conn
+                and self != other)
+
+    def holds(self, batch) -> bool:
+        return (len(batch) <= self.max_meshes and sum(r.n_elems for r in batch) <= self.max_elems
+                and sum(r.n_nodes for r in batch) <= self.max_nodes and sum(r.n_conn for r in batch) <= self.max_conn)
+
+
+# The small capacity class of every lane: a batch launch's fixed costs (its
+# bucket tables, scans and grids) follow the capacity it was captured for, so
+# a batch that fits runs on this class's own graph instead of the full one.
+SMALL_CAPS = LaneCaps(max_meshes=64, max_elems=2_500_000, max_nodes=2_500_000, max_conn=8_000_000)
+
 
 class ServeTimeout(RuntimeError):
     """A batch (or a plain build) whose completion event did not fire within
@@ -126,22 +145,18 @@ class Admission:
         return batch
 
 
-class _Lane:
-    def __init__(self, torch, caps: LaneCaps, device, want: int, use_graph: bool):
+class _Graph:
+    """One capacity class of a lane: a batch workspace and the CUDA graph
+    captured around its launch on the lane's stream."""
+
+    def __init__(self, torch, caps: LaneCaps, device, want: int, use_graph: bool, stream):
         self.torch = torch
-        self.stream = torch.cuda.Stream(device)
+        self.caps = caps
+        self.stream = stream
         self.bb = nn.BatchBuilder(caps.max_meshes, caps.max_elems, caps.max_nodes, caps.max_conn, want=want,
                                   device=device)
         self.graph = None
         self.use_graph = use_graph
-        self.event = torch.cuda.Event(enable_timing=True)
-        self.ev_start = torch.cuda.Event(enable_timing=True)
-        self.reqs = None
-        self.bufs = None
-        self.t_launch = 0.0    # host time the lane's current batch was enqueued
-
-    def workspace_bytes(self) -> int:
-        return self.bb.ws_bytes
 
     def launch(self):
         torch = self.torch
@@ -163,6 +178,79 @@ class _Lane:
             # the eager run already built this batch; replaying again is harmless
         with torch.cuda.stream(self.stream):
             self.graph.replay()
+
+
+class _Lane:
+    """A stream with its capacity classes (small first, then the lane's full
+    capacity; a batch of several requests runs on the smallest class that
+    holds it) and a single-mesh builder for a batch of one request, which
+    then starts at once with no batch tables."""
+
+    def __init__(self, torch, caps: LaneCaps, device, want: int, use_graph: bool):
+        self.torch = torch
+        self.want = want
+        self.stream = torch.cuda.Stream(device)
+        classes = [SMALL_CAPS] if SMALL_CAPS.holds_caps(caps) else []
+        self.classes = [_Graph(torch, c, device, want, use_graph, self.stream) for c in classes + [caps]]
+        self.single = nn.Builder(device)
+        self.single_status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.single_ws = None
+        self.single_ws_bytes = 0
+        self.event = torch.cuda.Event(enable_timing=True)
+        self.ev_start = torch.cuda.Event(enable_timing=True)
+        self.reqs = None
+        self.bufs = None
+        self.cls = None        # the class running the current batch (None: the single builder)
+        self.t_launch = 0.0    # host time the lane's current batch was enqueued
+
+    @property
+    def bb(self):
+        return (self.cls or self.classes[-1]).bb
+
+    def workspace_bytes(self) -> int:
+        return sum(g.bb.ws_bytes for g in self.classes)
+
+    def size_single(self, requests) -> int:
+        """Workspace of the single builder for the largest of `requests`
+        (grown, never shrunk; host sizing only).  Returns the bytes added."""
+        need = max((single_ws_bytes(self.single, r, self.want) for r in requests), default=0)
+        if need <= self.single_ws_bytes:
+            return 0
+        added = need - self.single_ws_bytes
+        self.single_ws = self.single.workspace(need)
+        self.single_ws_bytes = need
+        return added
+
+    def pick(self, batch):
+        self.cls = next(g for g in self.classes if g.caps.holds(batch))
+        return self.cls
+
+    def launch(self):
+        self.cls.launch()
+
+    def statuses(self, n: int) -> list:
+        if self.cls is None:
+            return self.single_status[:1].cpu().tolist()
+        return self.bb.status[:n].cpu().tolist()
+
+
+class _Sizes:
+    """A request's mesh sizes in the C ABI's mesh form, for host-only sizing
+    queries (the connectivity pointer is a placeholder no query reads)."""
+
+    def __init__(self, r: Request):
+        self.r = r
+
+    def struct(self):
+        r = self.r
+        return nn.NNMesh(type=r.etype, n_nodes=r.n_nodes, n_elems=r.n_elems, n_conn=r.n_conn, conn=256,
+                         elem_ptr=None, elem_type=None)
+
+
+def single_ws_bytes(builder, r: Request, want: int) -> int:
+    """Workspace of one single-mesh build of request `r` (host-only query on
+    the request's sizes)."""
+    return builder.query(_Sizes(r), want)[0]
 
 
 def _alloc_and_generate(torch, r: Request, device, stream, want):
@@ -211,8 +299,32 @@ class BatchServer:
         self.admission = Admission(self.caps)
         self.batches = 0
 
+    def warm(self, request: Request) -> None:
+        """Build `request` once on every capacity class of every lane, so that
+        every graph is captured before any timed run."""
+        torch = self.torch
+        for lane in self.lanes:
+            for g in lane.classes:
+                if not g.caps.holds([request]):
+                    continue
+                with torch.cuda.stream(lane.stream):
+                    dm, out = _alloc_and_generate(torch, request, self.device, lane.stream, self.want)
+                lane.cls = g
+                st = g.bb.prepare([dm], [out])
+                if st:
+                    raise nn.NNError(st, "nn_batch_prepare")
+                g.launch()
+                lane.stream.synchronize()
+                lane.cls = None
+
     def run(self, requests: List[Request]) -> dict:
         torch = self.torch
+        # the lanes' single builders sized for the largest request of the run
+        # (outside the timed loop; their workspace counts against the budget)
+        for lane in self.lanes:
+            self.budget -= lane.size_single([r for r in requests if self.admission.fits_alone(r)])
+        if self.budget <= 0:
+            raise ValueError("budget smaller than the lane workspaces")
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         queue, free, busy = deque(), list(self.lanes), []
         used = 0
@@ -230,7 +342,7 @@ class BatchServer:
             for lane in busy:
                 if lane.event.query():
                     t_done = ev0.elapsed_time(lane.event) * 1e-3
-                    stat = lane.bb.status[: len(lane.reqs)].cpu().tolist()
+                    stat = lane.statuses(len(lane.reqs))
                     t_start = ev0.elapsed_time(lane.ev_start) * 1e-3
                     for r, (dm, out), s in zip(lane.reqs, lane.bufs, stat):
                         r.t_done = t_done
@@ -253,12 +365,23 @@ class BatchServer:
                         bufs = [_alloc_and_generate(torch, r, self.device, lane.stream, self.want) for r in batch]
                     for r in batch:
                         used += r.device_bytes()
-                    st = lane.bb.prepare([d for d, _ in bufs], [o for _, o in bufs])
-                    if st:
-                        raise nn.NNError(st, "nn_batch_prepare")
-                    lane.ev_start.record(lane.stream)
-                    lane.t_launch = time.perf_counter()
-                    lane.launch()
+                    if len(batch) == 1:  # a lone request: the single-mesh build, no batch tables
+                        lane.cls = None
+                        lane.ev_start.record(lane.stream)
+                        lane.t_launch = time.perf_counter()
+                        (dm, out), = bufs
+                        st = lane.single.launch(dm, self.want, out, ws=lane.single_ws, ws_bytes=lane.single_ws_bytes,
+                                                stream=lane.stream, status=lane.single_status)
+                        if st:
+                            raise nn.NNError(st, "single build")
+                    else:
+                        lane.pick(batch)
+                        st = lane.bb.prepare([d for d, _ in bufs], [o for _, o in bufs])
+                        if st:
+                            raise nn.NNError(st, "nn_batch_prepare")
+                        lane.ev_start.record(lane.stream)
+                        lane.t_launch = time.perf_counter()
+                        lane.launch()
                     lane.event.record(lane.stream)
                     lane.reqs, lane.bufs = batch, bufs
                     busy.append(lane)

@@ -58,3 +58,16 @@ def test_request_bytes_cover_the_library_bounds():
             assert r.device_bytes() == 4 * r.n_conn + 2 * 8 * (r.n_nodes + 1) + 4 * (node_cap + elem_cap)
     finally:
         nn.nn_destroy(h)
+
+
+def test_capacity_classes_pick_the_smallest_that_holds_the_batch():
+    from paper_1604_04689_gb300.serve import SMALL_CAPS, LaneCaps, Request
+    full = LaneCaps()
+    assert SMALL_CAPS.holds_caps(full) and not full.holds_caps(full)
+    assert not SMALL_CAPS.holds_caps(LaneCaps(max_meshes=8))  # a lane smaller in any capacity gets no small class
+    small = [Request(i, 0, 100, i, 0.0) for i in range(3)]        # 3 triangle grids of 19,602 triangles
+    assert SMALL_CAPS.holds(small) and full.holds(small)
+    big = [Request(0, 3, 121, 0, 0.0)]                            # a hex grid of 1,728,000 hexes: 13.8 M entries
+    assert not SMALL_CAPS.holds(big) and full.holds(big)
+    many = [Request(i, 0, 10, i, 0.0) for i in range(SMALL_CAPS.max_meshes + 1)]
+    assert not SMALL_CAPS.holds(many) and full.holds(many)

@@ -65,6 +65,8 @@ class FakeBatchBuilder:
 
 
 class FakeBuilder:
+    launches = 0
+
     def __init__(self, device=None):
         pass
 
@@ -75,6 +77,7 @@ class FakeBuilder:
         return torch.empty(16, dtype=torch.uint8)
 
     def launch(self, dm, want, out, ws=None, ws_bytes=None, stream=None, status=None):
+        FakeBuilder.launches += 1
         stream.enqueue()
         return 0
 
@@ -95,6 +98,7 @@ def fake_cuda(monkeypatch):
     monkeypatch.setattr(nn, "generate_grid", fake_generate_grid)
     FakeStream.hang = False
     FakeBatchBuilder.launches = 0
+    FakeBuilder.launches = 0
     yield
     FakeStream.hang = False
 
@@ -115,7 +119,9 @@ def test_batch_server_serves_every_request(fake_cuda):
     assert st["requests"] == 40 and st["failed"] == 0 and st["rejected"] == 0
     assert all(r.t_done >= r.arrival for r in reqs)           # completion after arrival
     assert all(r.t_done >= r.t_start >= 0 for r in reqs)
-    assert st["batches"] == FakeBatchBuilder.launches and 5 <= st["batches"] <= 40   # at most 8 per batch
+    # a batch of one request runs as a single-mesh build on its lane, a larger one as a batch launch
+    assert st["batches"] == FakeBatchBuilder.launches + FakeBuilder.launches and 5 <= st["batches"] <= 40
+    assert FakeBatchBuilder.launches >= 1                      # at most 8 per batch
     assert st["max_ms"] >= st["p999_ms"] >= st["p99_ms"] >= st["p50_ms"] > 0
 
 
