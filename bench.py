@@ -322,12 +322,36 @@ LOCAL_EDGES = {0: ((0, 1), (1, 2), (2, 0)), 1: ((0, 1), (1, 2), (2, 3), (3, 0)),
                3: ((0, 1), (1, 2), (2, 3), (3, 0), (4, 5), (5, 6), (6, 7), (7, 4), (0, 4), (1, 5), (2, 6), (3, 7))}
 
 
+def sortpipe_build(torch, conn, etype, n_nodes):
+    """The paper's GPU recipe (Sec. 2.2.1) with library primitives: every
+    element of a uniform mesh (conn: int64 [T, npe] on the device) emits its
+    directed edge pairs (both orientations) and its (node, element) pairs as
+    64-bit keys; a radix sort orders them by key and unique-by-key gives the
+    rows, repeats dropped (the set reading of a one-ring).  Returns (rp_n,
+    col_n, rp_e, col_e).  Benchmark and test use only: it is the comparison
+    the paper's design makes possible, not a code path of the library."""
+    N, T = n_nodes, conn.shape[0]
+    dev = conn.device
+    eid = torch.arange(T, device=dev, dtype=torch.int64)
+    edges = LOCAL_EDGES[etype]
+    a = torch.cat([conn[:, i] for i, j in edges] + [conn[:, j] for i, j in edges])
+    b = torch.cat([conn[:, j] for i, j in edges] + [conn[:, i] for i, j in edges])
+    keep = a != b
+    keys = torch.sort((a * N + b)[keep]).values
+    u = torch.unique_consecutive(keys)
+    rp_n = torch.zeros(N + 1, dtype=torch.int64, device=dev)
+    rp_n[1:] = torch.cumsum(torch.bincount(u // N, minlength=N), 0)
+    col_n = (u % N).to(torch.int32)
+    ek = torch.unique_consecutive(torch.sort((conn * T + eid[:, None]).reshape(-1)).values)
+    rp_e = torch.zeros(N + 1, dtype=torch.int64, device=dev)
+    rp_e[1:] = torch.cumsum(torch.bincount(ek // T, minlength=N), 0)
+    col_e = (ek % T).to(torch.int32)
+    return rp_n, col_n, rp_e, col_e
+
+
 def sortpipe_arm(args):
-    """The paper's GPU recipe (Sec. 2.2.1) on this GPU with library primitives: every element emits its
-    directed edge pairs (both orientations) and its (node, element) pairs as 64-bit keys, a radix sort
-    orders them by key, and unique-by-key with counts gives the rows; duplicates are dropped (the set
-    reading of a one-ring).  Benchmark-only: it is the comparison the paper's design makes possible, not
-    a code path of the library.  Checked against the library's own build once, bit for bit."""
+    """--impl sortpipe: the paper's pipeline (sortpipe_build) timed on this
+    GPU, checked against the library's own build once, bit for bit."""
     import torch
     from paper_1604_04689_gb300 import nn
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
@@ -338,22 +362,9 @@ def sortpipe_arm(args):
         return
     N, T = mesh.n_nodes, mesh.n_elems
     conn = torch.from_numpy(mesh.conn).to(dev).view(T, -1).to(torch.int64)
-    eid = torch.arange(T, device=dev, dtype=torch.int64)
 
     def build():
-        a = torch.cat([conn[:, i] for i, j in LOCAL_EDGES[mesh.etype]] + [conn[:, j] for i, j in LOCAL_EDGES[mesh.etype]])
-        b = torch.cat([conn[:, j] for i, j in LOCAL_EDGES[mesh.etype]] + [conn[:, i] for i, j in LOCAL_EDGES[mesh.etype]])
-        keep = a != b
-        keys = torch.sort((a * N + b)[keep]).values
-        u = torch.unique_consecutive(keys)
-        rp_n = torch.zeros(N + 1, dtype=torch.int64, device=dev)
-        rp_n[1:] = torch.cumsum(torch.bincount(u // N, minlength=N), 0)
-        col_n = (u % N).to(torch.int32)
-        ek = torch.unique_consecutive(torch.sort((conn * T + eid[:, None]).reshape(-1)).values)
-        rp_e = torch.zeros(N + 1, dtype=torch.int64, device=dev)
-        rp_e[1:] = torch.cumsum(torch.bincount(ek // T, minlength=N), 0)
-        col_e = (ek % T).to(torch.int32)
-        return rp_n, col_n, rp_e, col_e
+        return sortpipe_build(torch, conn, mesh.etype, N)
 
     ref = nn.Builder(dev).build(nn.DeviceMesh.from_host(mesh, device=dev))
     got = build()

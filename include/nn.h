@@ -270,7 +270,8 @@ nn_status nn_batch_launch(nn_handle* h, const nn_batch_caps* caps, const void* s
  * memory that the call allocates; the stream frees it after the batch has
  * run (a host function enqueued on `stream`).  So the call is asynchronous
  * but cannot be captured in a CUDA graph: use nn_batch_prepare /
- * nn_batch_launch for that.  n_meshes == 0 enqueues nothing.  Host errors:
+ * nn_batch_launch for that; a stream that is capturing is refused with
+ * NN_ERR_ARG.  n_meshes == 0 enqueues nothing.  Host errors:
  * NN_ERR_ARG (bad mesh or pointers, no output wanted), NN_ERR_WORKSPACE
  * (ws_bytes below the minimum), NN_ERR_BUDGET (host memory for the staging
  * exhausted), NN_ERR_CUDA. */
@@ -313,7 +314,8 @@ nn_status nn_profile_read(nn_handle* h, double* ms, int64_t* calls, int n_stages
  * still passes the mesh, both output CSRs and d_status (all device memory it
  * owns) and the stream.  The first call on a device (with that device
  * current) looks up the array's device address; make that first call before
- * any stream capture.  Meshes whose build needs more scratch than the array
+ * any stream capture.  A call in a new context of the device (after
+ * cudaDeviceReset) looks the address up again.  Meshes whose build needs more scratch than the array
  * holds (roughly 1.5 million node-element incidences) are rejected with
  * NN_ERR_WORKSPACE before anything is enqueued.  All calls share the array
  * and it keeps the last call's contents: calls whose work overlaps on the GPU

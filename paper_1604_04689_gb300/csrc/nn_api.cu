@@ -32,6 +32,8 @@ struct nn_handle {
     int64_t calls = 0;
 };
 
+bool nn::handle_offline(const nn_handle* h) { return h && h->offline; }
+
 namespace {
 
 using namespace nn;

@@ -205,6 +205,7 @@ cudaError_t launch_batch_emit(const BatchTables& bt, uint32_t* bcount, uint32_t*
 int batch_threads();
 cudaError_t set_emit_smem_all(size_t bytes);
 cudaError_t set_bucket_smem_all(size_t bytes);
+bool handle_offline(const nn_handle* h);  // a sizing-only handle (nn_create_offline)
 nn_status build_with_limits(int sms, size_t smem_optin, size_t smem_per_sm, const nn_mesh* m, int want,
                             nn_csr* nodes, nn_csr* elems, void* ws, size_t ws_bytes, int32_t* d_status,
                             cudaStream_t s, size_t* ws_min);

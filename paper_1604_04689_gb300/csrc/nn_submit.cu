@@ -15,7 +15,7 @@
 
 #include <cuda_runtime.h>
 
-#include "nn.h"
+#include "nn_internal.h"
 
 namespace {
 
@@ -58,6 +58,12 @@ extern "C" nn_status nn_batch_submit(nn_handle* h, const nn_mesh* meshes, nn_csr
     nn_batch_caps c;
     nn_status st = caps_of(meshes, n_meshes, want, &c);
     if (st != NN_OK) return st;
+    if (nn::handle_offline(h)) return NN_ERR_ARG;
+    // the staging is freed by a host function on the stream: captured in a
+    // graph, every replay would free it again, so a capturing stream is refused
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(reinterpret_cast<cudaStream_t>(stream), &cap) != cudaSuccess) return NN_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return NN_ERR_ARG;
     size_t staging_bytes = 0;
     if ((st = nn_batch_query(h, &c, nullptr, &staging_bytes)) != NN_OK) return st;
     std::vector<uint64_t>* staging = nullptr;

@@ -191,3 +191,35 @@ def test_one_call_submit_equals_the_oracle(want):
                                                   err_msg=f"{m.name} {key} col")
     finally:
         nn.nn_destroy(h)
+
+
+def test_one_call_submit_refuses_a_capturing_stream():
+    """nn_batch_submit frees its host staging from the stream; captured into a
+    graph that would run on every replay, so a capturing stream is refused
+    with NN_ERR_ARG and nothing is enqueued (the captured graph stays empty)."""
+    import torch
+    h = nn.nn_create()
+    try:
+        meshes = batch_meshes(9)[:3]
+        dms = [nn.DeviceMesh.from_host(m) for m in meshes]
+        n = len(dms)
+        arr = (nn.NNMesh * n)(*[d.struct() for d in dms])
+        ws_bytes = nn.nn_batch_submit_query(h, arr, n, nn.WANT_ELEMS)
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+        status = torch.full((n,), -5, dtype=torch.int32, device="cuda")
+        outs = [(torch.full((d.n_nodes + 1,), -3, dtype=torch.int64, device="cuda"),
+                 torch.empty(max(d.n_conn, 1), dtype=torch.int32, device="cuda")) for d in dms]
+        elem_arr = (nn.NNCSR * n)(*[nn.NNCSR(rp.data_ptr(), col.data_ptr(), col.numel()) for rp, col in outs])
+        side = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            st = nn.nn_batch_submit(h, arr, None, elem_arr, n, ws.data_ptr(), ws_bytes, status.data_ptr(),
+                                    side.cuda_stream)
+        assert st == 1                               # NN_ERR_ARG
+        g.replay()                                   # the empty graph: nothing was captured
+        torch.cuda.synchronize()
+        assert status.cpu().tolist() == [-5] * n
+        assert all(int(rp[0].item()) == -3 for rp, _ in outs)
+    finally:
+        nn.nn_destroy(h)

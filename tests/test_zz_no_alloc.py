@@ -58,8 +58,11 @@ def test_noalloc_matches_workspace_entry_point(mesh_fn):
     ref = _host(torch, ref_out)
 
     status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    outs = [_outputs(torch, b, dm) for _ in range(2)]
+    torch.cuda.synchronize()
+    free_before = None
     for call in range(2):                                        # two calls in a row share the scratch
-        out = _outputs(torch, b, dm)
+        out = outs[call]
         for rp, col in out.values():                             # poison the outputs
             rp.fill_(-7)
             col.fill_(-7)
@@ -67,6 +70,13 @@ def test_noalloc_matches_workspace_entry_point(mesh_fn):
                                           status.data_ptr(), stream)
         assert st == 0, nn.STATUS.get(st, st)
         torch.cuda.synchronize()
+        # the first call of the process may load the library's code and with
+        # it the scratch array itself (lazy module loading); from then on a
+        # call takes no device memory
+        free_now = torch.cuda.mem_get_info()[0]
+        if free_before is not None:
+            assert free_now == free_before, f"call {call} took {free_before - free_now} bytes of device memory"
+        free_before = free_now
         assert int(status.item()) == 0, f"call {call}: device status {int(status.item())}"
         got = _host(torch, out)
         for k in ("nodes", "elems"):
@@ -80,7 +90,14 @@ def test_noalloc_rejects_meshes_beyond_the_scratch():
     dm = nn.DeviceMesh.from_host(mesh)
     b = nn.Builder()
     out = b.alloc_outputs(dm, nn.WANT_BOTH)
-    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    status = torch.full((1,), -9, dtype=torch.int32, device="cuda")  # poisoned: a call that enqueued would clear it
+    for rp, _ in out.values():
+        rp.fill_(-7)
+    torch.cuda.synchronize()
     st = nn.nn_neighbors_both_noalloc(dm.struct(), _csr(out["nodes"]), _csr(out["elems"]), status.data_ptr(),
                                       torch.cuda.current_stream().cuda_stream)
     assert st == 2                                               # NN_ERR_WORKSPACE, nothing enqueued
+    torch.cuda.synchronize()
+    assert int(status.item()) == -9
+    for rp, _ in out.values():
+        assert bool((rp == -7).all())
