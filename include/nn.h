@@ -66,7 +66,9 @@ typedef enum {
                               length / outside conn (device)                         */
     NN_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up (device)            */
     NN_ERR_BUDGET = 7,     /* serving layer: request larger than the memory budget   */
-    NN_ERR_CUDA = 8        /* a CUDA launch or driver call failed                    */
+    NN_ERR_CUDA = 8,       /* a CUDA launch or driver call failed                    */
+    NN_ERR_BOUNDS = 9      /* a bounds-checked build (libnn_checked.so) found an index
+                              outside its buffer and skipped the access (device)     */
 } nn_status;
 
 /* want flags */

@@ -355,6 +355,7 @@ nn_status enqueue(nn_handle* h, const nn_mesh* m, const Plan& p, nn_csr* nodes, 
     ep.rec = w + p.off_rec;
     ep.rec_cap = (uint64_t)p.n_conn;
     ep.status = d_status;
+    ep.hist_words = (uint64_t)p.G * (uint64_t)p.B;
 
     OffsetsParams op{};
     op.hist = ep.hist;
@@ -401,6 +402,10 @@ nn_status enqueue(nn_handle* h, const nn_mesh* m, const Plan& p, nn_csr* nodes, 
     bp.ntmp = reinterpret_cast<uint32_t*>(w + p.off_ntmp);
     bp.ubk = reinterpret_cast<uint32_t*>(w + p.off_ubk);
     bp.nloc = reinterpret_cast<uint32_t*>(w + p.off_nloc);
+    bp.rec_count = (uint64_t)p.n_conn;
+    bp.ntmp_words = (want & NN_WANT_NODES) ? (uint64_t)p.k * p.n_conn + 4 : 0;
+    bp.nloc_words = (want & NN_WANT_NODES) ? (uint64_t)p.B << p.fmt.sb : 0;
+    bp.ubk_words = (want & NN_WANT_NODES) ? (uint64_t)p.B : 0;
 
     mark(1);
     if (launch_hist(ep, p.emit_smem, s) != cudaSuccess) return NN_ERR_CUDA;
@@ -438,6 +443,8 @@ nn_status enqueue(nn_handle* h, const nn_mesh* m, const Plan& p, nn_csr* nodes, 
         cp.col_n = nodes->col;
         cp.cap_n = nodes->col_capacity;
         cp.status = d_status;
+        cp.ntmp_words = bp.ntmp_words;
+        cp.nloc_words = bp.nloc_words;
         if (launch_node_compact(cp, (int)std::min<int64_t>(p.B, (int64_t)h->sms * 8), s) != cudaSuccess)
             return NN_ERR_CUDA;
     }
@@ -644,6 +651,10 @@ nn_status batch_launch(nn_handle* h, const nn_batch_caps* c, const void* staging
     kp.ntmp = reinterpret_cast<uint32_t*>(w + bp.off_ntmp);
     kp.ubk = reinterpret_cast<uint32_t*>(w + bp.off_ubk);
     kp.nloc = reinterpret_cast<uint32_t*>(w + bp.off_nloc);
+    kp.rec_count = (uint64_t)c->max_conn;
+    kp.ntmp_words = (c->want & NN_WANT_NODES) ? 3 * (uint64_t)c->max_conn + 4 : 0;
+    kp.nloc_words = (c->want & NN_WANT_NODES) ? (uint64_t)bp.B_cap << bp.sb : 0;
+    kp.ubk_words = (c->want & NN_WANT_NODES) ? (uint64_t)bp.B_cap : 0;
     if (launch_bucket(kp, bp.bucket_grid, bp.bucket_threads, bp.bucket_smem, s) != cudaSuccess) return NN_ERR_CUDA;
     if (c->want & NN_WANT_NODES) {
         CompactParams cp{};
@@ -657,6 +668,8 @@ nn_status batch_launch(nn_handle* h, const nn_batch_caps* c, const void* staging
         cp.ticket = ctrl + 4;
         cp.status = reinterpret_cast<int32_t*>(ctrl + 8);
         cp.batch = bt;
+        cp.ntmp_words = kp.ntmp_words;
+        cp.nloc_words = kp.nloc_words;
         if (launch_node_compact(cp, h->sms * 8, s) != cudaSuccess) return NN_ERR_CUDA;
     }
     return NN_OK;
@@ -1075,6 +1088,7 @@ const char* nn_status_str(nn_status s) {
         case NN_ERR_TIMEOUT: return "device wait timed out";
         case NN_ERR_BUDGET: return "request exceeds memory budget";
         case NN_ERR_CUDA: return "CUDA error";
+        case NN_ERR_BOUNDS: return "index outside its buffer (checked build)";
     }
     return "unknown status";
 }

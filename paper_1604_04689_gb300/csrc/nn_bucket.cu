@@ -394,10 +394,16 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_bucket(BucketParams 
             const uint64_t R = M.r1 - M.r0;
             const uint64_t rb = rec_bytes(R, RB == 8 ? (M.r0 & 1u) * 8u : 0u, RB);
             M.sr = p.rec_smem && rb + 3 * word_bytes(R) <= A;
+#ifdef NN_CHECKED
+            const bool rec_ok = M.r1 >= M.r0 && M.r1 <= p.rec_count;  // else the bucket reads nothing
+            M.sr = M.sr && rec_ok;
+#else
+            constexpr bool rec_ok = true;
+#endif
             if (M.sr && rb <= limit) {
                 issue_copy(M);
                 M.copied = 1;
-            } else if (!M.sr) {
+            } else if (!M.sr && rec_ok) {
                 // read from global memory: start pulling the records into L2
                 uint64_t lo = (uint64_t)M.r0 * RB, hi = (uint64_t)M.r1 * RB;
                 lo &= ~15ull;
@@ -472,7 +478,13 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_bucket(BucketParams 
             if (tid == 0) set_status(sh_out.status, NN_ERR_TIMEOUT);
             return;
         }
-        const bool ok = top_in || misc[4] != 0;
+#ifdef NN_CHECKED
+        // the bucket's records lie inside the record array (else none is read)
+        const bool recs_in = M.r1 >= M.r0 && NN_IN((uint64_t)M.r1, p.rec_count + 1, sh_out.status);
+#else
+        constexpr bool recs_in = true;
+#endif
+        const bool ok = (top_in || misc[4] != 0) && recs_in;
         uint32_t* const Est = top_in ? reinterpret_cast<uint32_t*>(area + A - sbytes) : p.spill + misc[2];
         uint32_t* const grp = top_in ? reinterpret_cast<uint32_t*>(area + A - 2 * sbytes) : Est + sbytes / 4;
         uint8_t* const ust_top = area + (top_in ? A - 2 * sbytes : A);  // neighbour rows grow down from here
@@ -708,11 +720,11 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_bucket(BucketParams 
             s1 += t0;
             if (lane < NG) gpre[lane] = s0 - a0;
             if (lane + 32 < NG) gpre[lane + 32] = s1 - a1;
-            if (want_n && lane == 31) p.ubk[b] = s1;
+            if (want_n && lane == 31 && NN_IN(b, p.ubk_words, status)) p.ubk[b] = s1;
         } else if (want_e) {
             const bool e_ok = ok && M.ge + Eb <= (uint64_t)sh_out.cap_e;
             for (int l = tid - 32; l < nb; l += THREADS - 32)
-                sh_out.rp_e[v0 + l] = (int64_t)(M.ge + (uint32_t)(cnt[l] >> 32));
+                if (NN_IN(v0 + l, N + 1, status)) sh_out.rp_e[v0 + l] = (int64_t)(M.ge + (uint32_t)(cnt[l] >> 32));
             if (e_ok) {
                 int32_t* dst = sh_out.col_e + M.ge;
                 for (uint32_t i = tid - 32; i < Eb; i += THREADS - 32) dst[i] = (int32_t)Est[i];
@@ -721,18 +733,20 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_bucket(BucketParams 
         __syncthreads();
         if (want_n) {
             uint32_t* const loc = p.nloc + ((size_t)b << f.sb);
-            for (int l = tid; l < nb; l += THREADS) loc[l] = gpre[l >> 5] + c32[l];
+            for (int l = tid; l < nb; l += THREADS)
+                if (NN_IN(((size_t)b << f.sb) + l, p.nloc_words, status)) loc[l] = gpre[l >> 5] + c32[l];
             uint32_t* const rows = p.ntmp + (size_t)K * r0;
             for (int g = warp; ok && g < ng; g += W) {
                 const uint32_t seg = gseg[g], n = gtot[g];
                 if (seg == SEG_NONE) continue;
+                if (n && !NN_IN((size_t)K * r0 + gpre[g] + n - 1, p.ntmp_words, status)) continue;
                 const uint32_t* src = (seg & SEG_SPILL) ? p.spill + (seg & ~SEG_SPILL)
                                                         : reinterpret_cast<const uint32_t*>(ust_top) - seg;
                 uint32_t* dst = rows + gpre[g];
                 for (uint32_t i = lane; i < n; i += 32) dst[i] = src[i];
             }
         }
-        if (sh_out.last && tid == 0 && want_e) sh_out.rp_e[N] = (int64_t)(M.ge + Eb);
+        if (sh_out.last && tid == 0 && want_e && NN_IN(N, N + 1, status)) sh_out.rp_e[N] = (int64_t)(M.ge + Eb);
         __syncthreads();
         // the next bucket's copy, if it did not fit beside this one's rows
         if (tid == 0 && meta[(it + 1) & 1].sr && !meta[(it + 1) & 1].copied) issue_copy(meta[(it + 1) & 1]);

@@ -71,7 +71,8 @@ __global__ void __launch_bounds__(COPY_THREADS) k_node_copy(CompactParams p) {
         const int64_t v0 = (b - first) << sb;
         const int nb = (int)(N - v0 < ((int64_t)1 << sb) ? N - v0 : ((int64_t)1 << sb));
         const uint32_t* loc = p.nloc + ((size_t)b << sb);
-        for (int l = threadIdx.x; l < nb; l += COPY_THREADS) rp[v0 + l] = (int64_t)(gn + loc[l]);
+        for (int l = threadIdx.x; l < nb; l += COPY_THREADS)
+            if (NN_IN(((size_t)b << sb) + l, p.nloc_words, status)) rp[v0 + l] = (int64_t)(gn + loc[l]);
         if (last && threadIdx.x == 0) rp[N] = (int64_t)(gn + ub);
         if (gn + ub > (uint64_t)cap) {
             if (threadIdx.x == 0) set_status(status, NN_ERR_CAPACITY);
@@ -79,6 +80,7 @@ __global__ void __launch_bounds__(COPY_THREADS) k_node_copy(CompactParams p) {
         }
         const uint32_t* src = p.ntmp + (size_t)K * p.bstart[b];
         int32_t* dst = col + gn;
+        if (!NN_IN((size_t)K * p.bstart[b] + (ub ? ub - 1 : 0), p.ntmp_words + (ub ? 0 : 1), status)) continue;
         for (uint32_t i = threadIdx.x; i < ub; i += COPY_THREADS) dst[i] = (int32_t)__ldg(src + i);
     }
 }

@@ -15,6 +15,21 @@ constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 
 __device__ __forceinline__ void set_status(int32_t* st, int32_t code) { atomicCAS(st, 0, code); }
 
+// Bounds-checked build (compiled with -DNN_CHECKED into libnn_checked.so):
+// NN_IN(i, n, status) is false when index i lies outside a buffer of n
+// elements, after recording NN_ERR_BOUNDS; the caller then skips the access.
+// In the ordinary build it is the constant true and costs nothing.
+__device__ __forceinline__ bool in_bounds(uint64_t i, uint64_t n, int32_t* st) {
+    if (i < n) return true;
+    set_status(st, NN_ERR_BOUNDS);
+    return false;
+}
+#ifdef NN_CHECKED
+#define NN_IN(i, n, st) (::nn::in_bounds((uint64_t)(i), (uint64_t)(n), (st)))
+#else
+#define NN_IN(i, n, st) true
+#endif
+
 __device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
     uint64_t v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");

@@ -135,10 +135,12 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_hist(EmitParams p) {
             if (!node_in<RANGED>(p, v, vr)) return;  // another chunk's node
             const int64_t b = (int64_t)(vr >> sb) - c0;
             if (b >= 0 && b < nc) atomicAdd(&sh_hist[b], 1u);
-            if (nf && c0 == 0 && p.nfc) atomicAdd(&p.nfc[vr >> sb], 1u);  // rare: degenerate elements only
+            if (nf && c0 == 0 && p.nfc && NN_IN(vr >> sb, B, p.status))
+                atomicAdd(&p.nfc[vr >> sb], 1u);  // rare: degenerate elements only
         });
         __syncthreads();
-        for (int64_t b = threadIdx.x; b < nc; b += blockDim.x) row[c0 + b] = sh_hist[b];
+        for (int64_t b = threadIdx.x; b < nc; b += blockDim.x)
+            if (NN_IN((int64_t)blockIdx.x * B + c0 + b, p.hist_words, p.status)) row[c0 + b] = sh_hist[b];
         __syncthreads();
     }
 }
@@ -259,7 +261,8 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_part(EmitParams p) {
                 const int w = j / NPE, i = j % NPE;
                 pos[k][j] = 0xFFFFFFFFu;
                 uint32_t vr;
-                if (ok[k][w] && i < npe && node_in<RANGED>(p, nd[k][j], vr)) pos[k][j] = atomicAdd(&p.gcur[vr >> f.sb], 1u);
+                if (ok[k][w] && i < npe && node_in<RANGED>(p, nd[k][j], vr) && NN_IN(vr >> f.sb, p.n_buckets, p.status))
+                    pos[k][j] = atomicAdd(&p.gcur[vr >> f.sb], 1u);
             }
         }
 #pragma unroll
@@ -541,7 +544,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_part_fine(EmitParams p, const 
         __syncthreads();
         const uint32_t n_tile = tile_scan_n(hist, dof, nd_, sh_scan);
         for (int i = threadIdx.x; i < nd_; i += SORT_THREADS)
-            if (hist[i]) gbase[i] = atomicAdd(&p.gcur[fb0 + i], hist[i]);
+            if (hist[i] && NN_IN(fb0 + i, B, p.status)) gbase[i] = atomicAdd(&p.gcur[fb0 + i], hist[i]);
 #pragma unroll
         for (int k = 0; k < FINE_RPT; ++k) {
             if (rk[k] == 0xFFFF) continue;

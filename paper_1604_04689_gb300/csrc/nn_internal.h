@@ -59,6 +59,7 @@ struct EmitParams {
     uint8_t* rec;     // records, grouped by bucket
     uint64_t rec_cap; // records that fit; more only when elem_ptr is invalid
     int32_t* status;
+    uint64_t hist_words;  // length of hist (bounds-checked builds)
 };
 
 struct BatchHeader;
@@ -138,6 +139,11 @@ struct BucketParams {
     BatchTables batch;      // batch.hdr != nullptr: format, bucket count and meshes come from the tables
     const int32_t* batch_err;  // batches: status of the shared offsets scan, copied to every mesh
     const int64_t* base;    // chunked builds: {element-CSR, node-CSR} entries of the earlier chunks (else nullptr)
+    // buffer lengths, for bounds-checked builds
+    uint64_t rec_count;     // records the record array holds
+    uint64_t ntmp_words;    // words of ntmp
+    uint64_t nloc_words;    // words of nloc
+    uint64_t ubk_words;     // words of ubk
 };
 
 constexpr int EMIT_THREADS = 1024;
@@ -162,6 +168,9 @@ struct CompactParams {
     int32_t* status;
     BatchTables batch;
     const int64_t* base;     // chunked builds: {element-CSR, node-CSR} entries of the earlier chunks (else nullptr)
+    // buffer lengths, for bounds-checked builds
+    uint64_t ntmp_words;     // words of ntmp
+    uint64_t nloc_words;     // words of nloc
 };
 
 // Element face adjacency (nn_adj.cu).

@@ -29,7 +29,7 @@ LIB_PATH = os.path.join(HERE, "libnn.so")
 TRI, QUAD, TET, HEX, MIXED = 0, 1, 2, 3, 255
 WANT_NODES, WANT_ELEMS, WANT_BOTH = 1, 2, 3
 STATUS = {0: "NN_OK", 1: "NN_ERR_ARG", 2: "NN_ERR_WORKSPACE", 3: "NN_ERR_CAPACITY", 4: "NN_ERR_NODE_RANGE",
-          5: "NN_ERR_ELEM_PTR", 6: "NN_ERR_TIMEOUT", 7: "NN_ERR_BUDGET", 8: "NN_ERR_CUDA"}
+          5: "NN_ERR_ELEM_PTR", 6: "NN_ERR_TIMEOUT", 7: "NN_ERR_BUDGET", 8: "NN_ERR_CUDA", 9: "NN_ERR_BOUNDS"}
 NPE = {TRI: 3, QUAD: 4, TET: 4, HEX: 8}
 
 

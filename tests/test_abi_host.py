@@ -241,8 +241,8 @@ def test_generator_capacity_error_before_any_launch():
 # ------------------------------------------------------------ statuses, no fallback
 
 def test_every_status_has_its_own_text():
-    texts = [nn.lib().nn_status_str(s) for s in range(9)]
-    assert len(set(texts)) == 9 and all(texts)
+    texts = [nn.lib().nn_status_str(s) for s in range(10)]
+    assert len(set(texts)) == 10 and all(texts)
     assert nn.lib().nn_status_str(99) == b"unknown status"
 
 
