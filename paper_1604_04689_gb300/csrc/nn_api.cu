@@ -209,7 +209,7 @@ nn_status make_plan_range(const nn_handle* h, const nn_mesh* m, int want, int64_
     p.G_part = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sms * 2, (n_units + 511) / 512));
     if (f.cshift >= 0)  // tile-sorted passes: 256-thread CTAs, several per SM
         p.G_part = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sms * 4, (n_units + 511) / 512));
-    p.G_fine = h->sms * 4;
+    p.G_fine = h->sms;  // the fine pass sizes its grid by its occupancy
 
     p.area_words = (uint32_t)((p.bucket_smem - fixed_of(sb)) / 4);
     int per_sm = 1;

@@ -10,7 +10,9 @@
 // its bucket through one cursor per bucket, so the random global traffic is
 // one L2 atomic and one vector store per incidence, and the partially filled
 // sectors at the buckets' write heads (one per bucket) stay resident in L2.
-#include "nn_device.cuh"
+#include <algorithm>
+
+#include "nn_bulk.cuh"
 
 namespace nn {
 
@@ -357,9 +359,15 @@ __host__ __device__ constexpr size_t coarse_smem() {
 constexpr int FINE_RPT = 4;
 constexpr int FINE_TILE = SORT_THREADS * FINE_RPT;
 constexpr int FINE_DIGITS = 4096;  // buckets per coarse region: at most 256 x 4096 buckets in all
-// shared memory of the fine pass for nd digits per coarse region
-__host__ __device__ constexpr size_t fine_smem(int nd) { return (size_t)FINE_TILE * 18 + 3 * (size_t)nd * 4 + 257 * 4; }
-constexpr size_t FINE_SMEM = fine_smem(FINE_DIGITS);
+// shared memory of the fine pass for nd digits per coarse region and rb-byte
+// records: two tile stages (bulk-copy targets, 16 bytes of slack for an odd
+// 8-byte first record), the tile in digit order with its digits, three
+// per-digit tables and the first work item of every coarse region
+__host__ __device__ constexpr size_t fine_stage_bytes(int rb) { return (size_t)FINE_TILE * rb + 16; }
+__host__ __device__ constexpr size_t fine_smem(int nd, int rb) {
+    return 2 * fine_stage_bytes(rb) + (size_t)FINE_TILE * 18 + 3 * (size_t)nd * 4 + 257 * 4;
+}
+constexpr size_t FINE_SMEM = fine_smem(FINE_DIGITS, 16);
 
 // vr: the node's id relative to the build's first node
 template <int TYPE>
@@ -477,11 +485,17 @@ __global__ void __launch_bounds__(SORT_THREADS) k_part_coarse(EmitParams p) {
 }
 
 // Second pass: one coarse region per work item group; radix digit = bucket
-// inside the region (stored in the record by the first pass).
+// inside the region (stored in the record by the first pass).  A CTA's work
+// items are tiles of FINE_TILE records; each tile is brought into shared
+// memory by a bulk asynchronous copy issued while the CTA still sorts and
+// writes the tile before it (two stages, one mbarrier each, bounded waits),
+// so the tile loads overlap the in-tile sort instead of stalling it.
 template <int RB>
 __global__ void __launch_bounds__(SORT_THREADS) k_part_fine(EmitParams p, const uint32_t* bstart) {
     extern __shared__ __align__(16) uint8_t sm[];
-    ulonglong2* out = reinterpret_cast<ulonglong2*>(sm);
+    constexpr uint32_t SB = (uint32_t)fine_stage_bytes(RB);
+    uint8_t* const stage = sm;  // [2][SB]
+    ulonglong2* out = reinterpret_cast<ulonglong2*>(sm + 2 * SB);
     uint16_t* odig = reinterpret_cast<uint16_t*>(out + FINE_TILE);
     const RecFmt f = p.fmt;
     const int cs = f.cshift;
@@ -491,6 +505,9 @@ __global__ void __launch_bounds__(SORT_THREADS) k_part_fine(EmitParams p, const 
     uint32_t* gbase = dof + nd_;
     uint32_t* tpre = gbase + nd_;  // [257] first tile of each coarse region
     __shared__ uint64_t sh_scan[34];
+    __shared__ uint64_t mbar[2];
+    __shared__ uint32_t sh_tile[2][4];  // per stage: region, first record, end, offset of record 0 in the stage
+    __shared__ int32_t sh_lost;
     const int64_t B = p.n_buckets;
     const int R1 = (int)((B + (1ll << cs) - 1) >> cs);
     const int d0 = threadIdx.x;
@@ -507,9 +524,16 @@ __global__ void __launch_bounds__(SORT_THREADS) k_part_fine(EmitParams p, const 
         if (d0 < R1) tpre[d0] = (uint32_t)ex;
         if (d0 == 0) tpre[R1] = (uint32_t)total;
     }
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0]);
+        mbar_init(&mbar[1]);
+        sh_lost = 0;
+    }
     __syncthreads();
     const uint32_t W = tpre[R1];
-    for (uint32_t wi = blockIdx.x; wi < W; wi += gridDim.x) {
+    // One thread: locate work item wi and start the copy of its records
+    // into stage st (stage st is free: its previous tile passed a barrier).
+    auto issue = [&](int st, uint32_t wi) {
         int lo = 0, hi = R1;  // largest d with tpre[d] <= wi
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -522,25 +546,60 @@ __global__ void __launch_bounds__(SORT_THREADS) k_part_fine(EmitParams p, const 
         const uint32_t ra = bstart[fb0], rb_ = bstart[fe < B ? fe : B];
         const uint32_t r0 = ra + (wi - tpre[d]) * FINE_TILE;
         const uint32_t r1 = min(r0 + (uint32_t)FINE_TILE, rb_);
+        const uint32_t roff = RB == 8 ? (r0 & 1u) * 8u : 0u;
+        sh_tile[st][0] = (uint32_t)d;
+        sh_tile[st][1] = r0;
+        sh_tile[st][2] = r1;
+        sh_tile[st][3] = roff;
+        if (r1 > r0) {
+            // the coarse-sorted records are padded to 256 bytes, so the rounded-up tail stays inside them
+            const uint32_t bytes = ((r1 - r0) * RB + roff + 15u) & ~15u;
+            fence_async_smem();
+            mbar_expect(&mbar[st], bytes);
+            bulk_load(stage + st * SB, p.rec_tmp + (uint64_t)r0 * RB - roff, bytes, &mbar[st]);
+        }
+    };
+    if (threadIdx.x == 0 && blockIdx.x < W) issue(0, blockIdx.x);
+    uint32_t par[2] = {0u, 0u};  // parity of each stage's next copy
+    int it = 0;
+    for (uint32_t wi = blockIdx.x; wi < W; wi += gridDim.x, ++it) {
+        const int st = it & 1;
+        // the next tile of this CTA, into the other stage
+        if (threadIdx.x == 0 && wi + gridDim.x < W) issue(st ^ 1, wi + gridDim.x);
         for (int i = threadIdx.x; i < nd_; i += SORT_THREADS) hist[i] = 0;
+        // thread 0 issued this stage's copy and waits for it; the others wait
+        // at the barrier, after which the stage's records and bounds are seen
+        if (threadIdx.x == 0 && sh_tile[st][2] > sh_tile[st][1]) {
+            if (!mbar_wait(&mbar[st], par[st])) sh_lost = 1;
+            par[st] ^= 1u;
+        }
         __syncthreads();
+        if (sh_lost) {  // a copy that never completed (bounded wait): report and stop
+            if (threadIdx.x == 0) set_status(p.status, NN_ERR_TIMEOUT);
+            return;
+        }
+        const int d = (int)sh_tile[st][0];
+        const int64_t fb0 = (int64_t)d << cs;
+        const uint32_t n = sh_tile[st][2] - sh_tile[st][1];
+        const uint8_t* const src = stage + st * SB + sh_tile[st][3];
         ulonglong2 x[FINE_RPT];
         uint16_t rk[FINE_RPT];
         uint16_t dg[FINE_RPT];
 #pragma unroll
         for (int k = 0; k < FINE_RPT; ++k) {
-            const uint32_t r = r0 + threadIdx.x + k * SORT_THREADS;
+            const uint32_t r = threadIdx.x + k * SORT_THREADS;
             rk[k] = 0xFFFF;
             dg[k] = 0;
-            if (r < r1) {
-                x[k] = load_rec2<RB>(p.rec_tmp, r);
+            if (r < n) {
+                if constexpr (RB == 8) x[k] = make_ulonglong2(reinterpret_cast<const unsigned long long*>(src)[r], 0);
+                else x[k] = reinterpret_cast<const ulonglong2*>(src)[r];
                 const Rec rr{x[k].x, x[k].y};
                 dg[k] = (uint16_t)rec_get(rr, f.off_fb, cs);
             }
         }
 #pragma unroll
         for (int k = 0; k < FINE_RPT; ++k)
-            if (r0 + threadIdx.x + k * SORT_THREADS < r1) rk[k] = (uint16_t)atomicAdd(&hist[dg[k]], 1u);
+            if (threadIdx.x + k * SORT_THREADS < n) rk[k] = (uint16_t)atomicAdd(&hist[dg[k]], 1u);
         __syncthreads();
         const uint32_t n_tile = tile_scan_n(hist, dof, nd_, sh_scan);
         for (int i = threadIdx.x; i < nd_; i += SORT_THREADS)
@@ -695,18 +754,27 @@ cudaError_t launch_part_coarse(const EmitParams& p, cudaStream_t s) {
     }
 }
 
-cudaError_t launch_part_fine(const EmitParams& p, const uint32_t* bstart, int grid_fine, cudaStream_t s) {
-    if (p.fmt.cshift <= 0) return cudaSuccess;
-    const size_t fs = fine_smem(1 << p.fmt.cshift);
-    if (p.fmt.rb == 8) k_part_fine<8><<<grid_fine, SORT_THREADS, fs, s>>>(p, bstart);
-    else k_part_fine<16><<<grid_fine, SORT_THREADS, fs, s>>>(p, bstart);
+// One CTA per resident slot (the SMs times the CTAs its shared memory
+// allows per SM): each CTA works through its tiles with the copies in flight.
+template <int RB>
+cudaError_t fine_t(const EmitParams& p, const uint32_t* bstart, int sms, cudaStream_t s) {
+    const size_t fs = fine_smem(1 << p.fmt.cshift, RB);
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_part_fine<RB>, SORT_THREADS, fs);
+    if (e != cudaSuccess) return e;
+    k_part_fine<RB><<<std::max(1, sms * std::max(occ, 1)), SORT_THREADS, fs, s>>>(p, bstart);
     return cudaGetLastError();
 }
 
-cudaError_t launch_part_sorted(const EmitParams& p, const uint32_t* bstart, int grid_fine, cudaStream_t s) {
+cudaError_t launch_part_fine(const EmitParams& p, const uint32_t* bstart, int sms, cudaStream_t s) {
+    if (p.fmt.cshift <= 0) return cudaSuccess;
+    return p.fmt.rb == 8 ? fine_t<8>(p, bstart, sms, s) : fine_t<16>(p, bstart, sms, s);
+}
+
+cudaError_t launch_part_sorted(const EmitParams& p, const uint32_t* bstart, int sms, cudaStream_t s) {
     cudaError_t e = launch_part_coarse(p, s);
     if (e != cudaSuccess) return e;
-    return launch_part_fine(p, bstart, grid_fine, s);
+    return launch_part_fine(p, bstart, sms, s);
 }
 
 template <int TYPE>

@@ -200,10 +200,10 @@ cudaError_t launch_chunk_advance(int64_t* base, const uint32_t* estart, const ui
 cudaError_t launch_slab_count(const EmitParams& p, int shift, int n_slabs, uint32_t* counts, cudaStream_t s);
 cudaError_t launch_hist(const EmitParams& p, size_t smem, cudaStream_t s);
 cudaError_t launch_part(const EmitParams& p, cudaStream_t s);
-cudaError_t launch_part_sorted(const EmitParams& p, const uint32_t* bstart, int grid_fine, cudaStream_t s);
+cudaError_t launch_part_sorted(const EmitParams& p, const uint32_t* bstart, int sms, cudaStream_t s);
 // the two passes of launch_part_sorted on their own (the fine pass only when cshift > 0)
 cudaError_t launch_part_coarse(const EmitParams& p, cudaStream_t s);
-cudaError_t launch_part_fine(const EmitParams& p, const uint32_t* bstart, int grid_fine, cudaStream_t s);
+cudaError_t launch_part_fine(const EmitParams& p, const uint32_t* bstart, int sms, cudaStream_t s);
 cudaError_t launch_offsets(const OffsetsParams& p, cudaStream_t s);
 cudaError_t launch_bucket(const BucketParams& p, int grid, int threads, size_t smem, cudaStream_t s);
 size_t bucket_fixed_bytes(int sb, int threads, int wide);  // shared memory of the bucket kernel outside its area

@@ -1,21 +1,24 @@
 """Serving loop: continuous batching of neighbour-CSR build requests.
 
 Requests (a seeded grid mesh: type, grid side, seed) arrive over time.  The
-batched server keeps ``lanes`` independent lanes (a CUDA stream, batch
-workspaces of a small and of the full capacity, pinned staging and a CUDA
-graph captured once around each batched launch, and a single-mesh builder).
-Whenever a lane is free it admits the requests that have arrived, in arrival
-order, while they fit the lane's capacity and the device-memory budget,
-materialises their connectivity on the lane's stream (device generator, the
-stand-in for an upload), and either builds a lone request at once with the
-single-mesh builder or prepares the batch tables and replays the graph of the
-smallest capacity that holds the batch.  While one lane's batch runs on the
-GPU, the next batch is admitted and launched on another lane, so work
-overlaps on the device and requests are admitted as lanes and memory free
-up.  The plain server
-answers the same requests one build call per mesh on one stream.
+batched server owns ``streams`` CUDA streams, a single-mesh builder per
+stream and ``lanes`` batch slots (a slot: batch workspaces of a small and of
+the full capacity, pinned staging and a CUDA graph captured once around each
+batched launch).  Work goes to the streams as units; each stream holds at
+most ``depth`` units in flight, and a new unit goes to the open stream with
+the fewest elements in flight.  Whenever a stream is open, the requests that
+have arrived are admitted at once: fewer than ``batch_min`` waiting requests
+leave one by one as single-mesh builds; ``batch_min`` or more leave together
+as one batch on a free slot (in arrival order, while they fit the slot's
+capacity and the device-memory budget).  So a lightly loaded server answers
+each request as soon as it arrives, with small requests running beside large
+ones instead of behind them, and a loaded one amortises the launch sequence
+over every request that queued while all streams were busy.  Each request's
+connectivity is materialised on its stream (device generator, the stand-in
+for an upload).  The plain server answers the same requests one build call
+per mesh on one stream.
 
-Latency of a request = completion (CUDA event at the end of its batch, mapped
+Latency of a request = completion (CUDA event at the end of its unit, mapped
 to the host clock) - arrival.  Results are identical whether a request is
 built alone or in a batch (see tests/test_gpu_serve.py).
 """
@@ -128,10 +131,11 @@ class Admission:
         c = self.caps
         return r.n_elems <= c.max_elems and r.n_nodes <= c.max_nodes and r.n_conn <= c.max_conn
 
-    def form(self, queue: deque, free_bytes: int) -> list:
+    def form(self, queue: deque, free_bytes: int, limit: Optional[int] = None) -> list:
         c = self.caps
+        cap = c.max_meshes if limit is None else min(limit, c.max_meshes)
         batch, e, nn_, cc, b = [], 0, 0, 0, 0
-        while queue and len(batch) < c.max_meshes:
+        while queue and len(batch) < cap:
             r = queue[0]
             if (e + r.n_elems > c.max_elems or nn_ + r.n_nodes > c.max_nodes or cc + r.n_conn > c.max_conn
                     or b + r.device_bytes() > free_bytes):
@@ -181,27 +185,20 @@ class _Graph:
 
 
 class _Lane:
-    """A stream with its capacity classes (small first, then the lane's full
-    capacity; a batch of several requests runs on the smallest class that
-    holds it) and a single-mesh builder for a batch of one request, which
-    then starts at once with no batch tables."""
+    """A batch slot: its capacity classes (small first, then the slot's full
+    capacity; a batch runs on the smallest class that holds it), each with a
+    batch workspace, pinned staging and a graph captured on the server's
+    stream.  A slot takes a new batch once its previous one has completed, so
+    its staging is never rewritten while a launch may still read it."""
 
-    def __init__(self, torch, caps: LaneCaps, device, want: int, use_graph: bool):
+    def __init__(self, torch, caps: LaneCaps, device, want: int, use_graph: bool, stream):
         self.torch = torch
         self.want = want
-        self.stream = torch.cuda.Stream(device)
+        self.stream = stream
         classes = [SMALL_CAPS] if SMALL_CAPS.holds_caps(caps) else []
         self.classes = [_Graph(torch, c, device, want, use_graph, self.stream) for c in classes + [caps]]
-        self.single = nn.Builder(device)
-        self.single_status = torch.zeros(1, dtype=torch.int32, device=device)
-        self.single_ws = None
-        self.single_ws_bytes = 0
-        self.event = torch.cuda.Event(enable_timing=True)
-        self.ev_start = torch.cuda.Event(enable_timing=True)
-        self.reqs = None
-        self.bufs = None
-        self.cls = None        # the class running the current batch (None: the single builder)
-        self.t_launch = 0.0    # host time the lane's current batch was enqueued
+        self.cls = None        # the class running the slot's current batch
+        self.busy = False
 
     @property
     def bb(self):
@@ -210,28 +207,12 @@ class _Lane:
     def workspace_bytes(self) -> int:
         return sum(g.bb.ws_bytes for g in self.classes)
 
-    def size_single(self, requests) -> int:
-        """Workspace of the single builder for the largest of `requests`
-        (grown, never shrunk; host sizing only).  Returns the bytes added."""
-        need = max((single_ws_bytes(self.single, r, self.want) for r in requests), default=0)
-        if need <= self.single_ws_bytes:
-            return 0
-        added = need - self.single_ws_bytes
-        self.single_ws = self.single.workspace(need)
-        self.single_ws_bytes = need
-        return added
-
     def pick(self, batch):
         self.cls = next(g for g in self.classes if g.caps.holds(batch))
         return self.cls
 
     def launch(self):
         self.cls.launch()
-
-    def statuses(self, n: int) -> list:
-        if self.cls is None:
-            return self.single_status[:1].cpu().tolist()
-        return self.bb.status[:n].cpu().tolist()
 
 
 class _Sizes:
@@ -284,7 +265,7 @@ def _stats(reqs: List[Request], t_first: float, t_last: float) -> dict:
 class BatchServer:
     def __init__(self, budget_bytes: int = 40 << 30, lanes: int = 2, caps: Optional[LaneCaps] = None,
                  want: int = nn.WANT_BOTH, device=None, use_graph: bool = True, keep_results: bool = False,
-                 deadline_s: float = 60.0):
+                 deadline_s: float = 60.0, streams: int = 2, depth: int = 2, batch_min: int = 8):
         import torch
         self.torch = torch
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -292,15 +273,34 @@ class BatchServer:
         self.caps = caps or LaneCaps()
         self.want = want
         self.keep = keep_results
-        self.lanes = [_Lane(torch, self.caps, self.device, want, use_graph) for _ in range(lanes)]
+        self.depth = max(1, depth)          # units in flight per stream
+        self.batch_min = max(2, batch_min)  # queued requests that make a batch (fewer: the oldest alone)
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(max(1, streams))]
+        self.lanes = [_Lane(torch, self.caps, self.device, want, use_graph, self.streams[i % len(self.streams)])
+                      for i in range(lanes)]
+        self.singles = [nn.Builder(self.device) for _ in self.streams]
+        self.single_ws = [None] * len(self.streams)
+        self.single_ws_bytes = 0
         self.budget = budget_bytes - sum(l.workspace_bytes() for l in self.lanes)
         if self.budget <= 0:
             raise ValueError("budget smaller than the lane workspaces")
         self.admission = Admission(self.caps)
         self.batches = 0
 
+    def size_single(self, requests) -> int:
+        """Workspace of each stream's single-mesh builder for the largest of
+        `requests` (grown, never shrunk; host sizing only).  Returns the bytes
+        added."""
+        need = max((single_ws_bytes(self.singles[0], r, self.want) for r in requests), default=0)
+        if need <= self.single_ws_bytes:
+            return 0
+        added = (need - self.single_ws_bytes) * len(self.streams)
+        self.single_ws = [b.workspace(need) for b in self.singles]
+        self.single_ws_bytes = need
+        return added
+
     def warm(self, request: Request) -> None:
-        """Build `request` once on every capacity class of every lane, so that
+        """Build `request` once on every capacity class of every slot, so that
         every graph is captured before any timed run."""
         torch = self.torch
         for lane in self.lanes:
@@ -319,78 +319,108 @@ class BatchServer:
 
     def run(self, requests: List[Request]) -> dict:
         torch = self.torch
-        # the lanes' single builders sized for the largest request of the run
-        # (outside the timed loop; their workspace counts against the budget)
-        for lane in self.lanes:
-            self.budget -= lane.size_single([r for r in requests if self.admission.fits_alone(r)])
+        # the single-mesh builders sized for the largest request of the run
+        # (outside the timed loop; their workspaces count against the budget)
+        self.budget -= self.size_single([r for r in requests if self.admission.fits_alone(r)])
         if self.budget <= 0:
             raise ValueError("budget smaller than the lane workspaces")
         pending = deque(sorted(requests, key=lambda r: r.arrival))
-        queue, free, busy = deque(), list(self.lanes), []
+        queue, inflight = deque(), []
+        load = [0] * len(self.streams)   # units in flight per stream
+        work = [0] * len(self.streams)   # their elements: a unit goes to the least loaded stream
+        # statuses: each unit writes those of its requests at their admission
+        # positions, on its stream (read once, after the run)
+        status = torch.zeros(max(len(requests), 1), dtype=torch.int32, device=self.device)
+        admitted = []
         used = 0
         ev0 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(self.device)
         ev0.record(torch.cuda.current_stream(self.device))
         t0 = time.perf_counter()
         rejected = []
-        while pending or queue or busy:
+        while pending or queue or inflight:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
                 r = pending.popleft()
                 (queue if self.admission.fits_alone(r) else rejected).append(r)
             still = []
-            for lane in busy:
-                if lane.event.query():
-                    t_done = ev0.elapsed_time(lane.event) * 1e-3
-                    stat = lane.statuses(len(lane.reqs))
-                    t_start = ev0.elapsed_time(lane.ev_start) * 1e-3
-                    for r, (dm, out), s in zip(lane.reqs, lane.bufs, stat):
+            for u in inflight:
+                if u["done"].query():
+                    t_done = ev0.elapsed_time(u["done"]) * 1e-3
+                    t_start = ev0.elapsed_time(u["start"]) * 1e-3
+                    for r, (dm, out) in zip(u["reqs"], u["bufs"]):
                         r.t_done = t_done
                         r.t_start = t_start
-                        r.status = int(s)
                         if self.keep:
                             r.result = {k: (rp, col) for k, (rp, col) in out.items()}
                         used -= r.device_bytes()
-                    lane.reqs = lane.bufs = None
-                    free.append(lane)
+                    if u["lane"] is not None:
+                        u["lane"].busy = False
+                    load[u["si"]] -= 1
+                    work[u["si"]] -= sum(r.n_elems for r in u["reqs"])
                 else:
-                    check_deadline(lane.t_launch, self.deadline_s, f"batch of {len(lane.reqs)} requests")
-                    still.append(lane)
-            busy = still
-            if free and queue:
-                batch = self.admission.form(queue, self.budget - used)
+                    check_deadline(u["t_launch"], self.deadline_s, f"unit of {len(u['reqs'])} requests")
+                    still.append(u)
+            inflight = still
+            open_ = [i for i in range(len(self.streams)) if load[i] < self.depth]
+            si = min(open_, key=lambda i: work[i]) if open_ else 0
+            if queue and open_:
+                s = self.streams[si]
+                lane = next((l for l in self.lanes if not l.busy and l.stream is s), None)
+                if lane is None:
+                    lane = next((l for l in self.lanes if not l.busy), None)
+                many = len(queue) >= self.batch_min and lane is not None
+                batch = self.admission.form(queue, self.budget - used, limit=None if many else 1)
                 if batch:
-                    lane = free.pop()
-                    with torch.cuda.stream(lane.stream):
-                        bufs = [_alloc_and_generate(torch, r, self.device, lane.stream, self.want) for r in batch]
+                    k0 = len(admitted)
+                    admitted.extend(batch)
+                    with torch.cuda.stream(s):
+                        bufs = [_alloc_and_generate(torch, r, self.device, s, self.want) for r in batch]
                     for r in batch:
                         used += r.device_bytes()
+                    ev_start, ev_done = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     if len(batch) == 1:  # a lone request: the single-mesh build, no batch tables
-                        lane.cls = None
-                        lane.ev_start.record(lane.stream)
-                        lane.t_launch = time.perf_counter()
+                        lane = None
+                        ev_start.record(s)
                         (dm, out), = bufs
-                        st = lane.single.launch(dm, self.want, out, ws=lane.single_ws, ws_bytes=lane.single_ws_bytes,
-                                                stream=lane.stream, status=lane.single_status)
+                        st = self.singles[si].launch(dm, self.want, out, ws=self.single_ws[si],
+                                                     ws_bytes=self.single_ws_bytes, stream=s,
+                                                     status=status[k0:k0 + 1])
                         if st:
                             raise nn.NNError(st, "single build")
                     else:
+                        if lane.stream is not s:  # the slot's graph replays on its own stream
+                            ev_in = torch.cuda.Event()
+                            ev_in.record(s)
+                            lane.stream.wait_event(ev_in)
                         lane.pick(batch)
                         st = lane.bb.prepare([d for d, _ in bufs], [o for _, o in bufs])
                         if st:
                             raise nn.NNError(st, "nn_batch_prepare")
-                        lane.ev_start.record(lane.stream)
-                        lane.t_launch = time.perf_counter()
+                        ev_start.record(lane.stream)
                         lane.launch()
-                    lane.event.record(lane.stream)
-                    lane.reqs, lane.bufs = batch, bufs
-                    busy.append(lane)
+                        lane.busy = True
+                        with torch.cuda.stream(lane.stream):
+                            status[k0:k0 + len(batch)].copy_(lane.bb.status[:len(batch)], non_blocking=True)
+                        if lane.stream is not s:
+                            ev_out = torch.cuda.Event()
+                            ev_out.record(lane.stream)
+                            s.wait_event(ev_out)
+                    ev_done.record(s)
+                    load[si] += 1
+                    work[si] += sum(r.n_elems for r in batch)
+                    inflight.append(dict(reqs=batch, bufs=bufs, start=ev_start, done=ev_done, lane=lane, si=si,
+                                         t_launch=time.perf_counter()))
                     self.batches += 1
                     continue
-            if not busy and not queue and pending:
+            if not inflight and not queue and pending:
                 time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 0.001)))
-            elif busy:
+            elif inflight:
                 time.sleep(20e-6)
+        torch.cuda.synchronize(self.device)
+        st_all = status.cpu().tolist()
+        for i, r in enumerate(admitted):
+            r.status = int(st_all[i])
         for r in rejected:
             r.status = 7  # NN_ERR_BUDGET: larger than an empty lane
         served = [r for r in requests if r.t_done >= 0]

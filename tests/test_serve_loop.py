@@ -1,9 +1,10 @@
 """The serving loops' host logic on the CPU: BatchServer and PlainServer run
 their real event loops against fake CUDA streams, events and builders (each
-"GPU" batch completes a fixed time after it is enqueued), so admission across
-lanes, completion bookkeeping, rejection of oversized requests and the
-statistics are checked without a GPU; and a stream that never completes
-trips the host watchdog instead of spinning forever."""
+"GPU" unit completes a fixed time after it is enqueued behind the stream's
+earlier work), so admission, the in-flight depth, completion bookkeeping,
+rejection of oversized requests and the statistics are checked without a
+GPU; and a stream that never completes trips the host watchdog instead of
+spinning forever."""
 import contextlib
 import time
 
@@ -26,6 +27,10 @@ class FakeStream:
 
     def enqueue(self):
         self.busy_until = max(self.busy_until, time.perf_counter()) + GPU_S
+
+    def wait_event(self, ev):
+        if ev.t is not None:
+            self.busy_until = max(self.busy_until, ev.t)
 
 
 class FakeEvent:
@@ -119,10 +124,50 @@ def test_batch_server_serves_every_request(fake_cuda):
     assert st["requests"] == 40 and st["failed"] == 0 and st["rejected"] == 0
     assert all(r.t_done >= r.arrival for r in reqs)           # completion after arrival
     assert all(r.t_done >= r.t_start >= 0 for r in reqs)
-    # a batch of one request runs as a single-mesh build on its lane, a larger one as a batch launch
+    # a lone request runs as a single-mesh build, several as one batch launch
     assert st["batches"] == FakeBatchBuilder.launches + FakeBuilder.launches and 5 <= st["batches"] <= 40
     assert FakeBatchBuilder.launches >= 1                      # at most 8 per batch
     assert st["max_ms"] >= st["p999_ms"] >= st["p99_ms"] >= st["p50_ms"] > 0
+
+
+def test_batch_server_light_load_builds_each_request_alone(fake_cuda):
+    # arrivals further apart than a unit's device time: every request finds
+    # the stream below its depth and is built at once, on its own
+    reqs = [Request(i, (mg.TRI, mg.TET, mg.HEX)[i % 3], 4, i, i * 3 * GPU_S) for i in range(12)]
+    srv = BatchServer(budget_bytes=1 << 30, lanes=2, caps=LaneCaps(max_meshes=8), device="cpu", use_graph=False)
+    st = srv.run(reqs)
+    assert st["failed"] == 0 and st["batches"] == 12
+    assert FakeBuilder.launches == 12 and FakeBatchBuilder.launches == 0
+    assert all(r.t_done - r.arrival < 2.5 * GPU_S for r in reqs)
+
+
+def test_batch_server_holds_arrivals_beyond_its_depth_for_one_batch(fake_cuda):
+    # one stream, two units in flight: a burst leaves as batches of at most
+    # max_meshes while both slots are free, the remainder once a unit completes
+    reqs = [Request(i, mg.TRI, 4, i, 0.0) for i in range(20)]
+    srv = BatchServer(budget_bytes=1 << 30, lanes=2, caps=LaneCaps(max_meshes=8), device="cpu", use_graph=False,
+                      streams=1, depth=2, batch_min=2)
+    st = srv.run(reqs)
+    assert st["failed"] == 0 and st["requests"] == 20
+    assert FakeBatchBuilder.launches == 3 and FakeBuilder.launches == 0 and st["batches"] == 3   # 8 + 8 + 4
+    # one stream: units complete in the order they were admitted
+    done = [r.t_done for r in reqs]
+    assert done == sorted(done)
+
+
+def test_batch_server_small_queues_go_alone_on_the_least_loaded_stream(fake_cuda):
+    # fewer queued requests than batch_min: each leaves alone, spread over
+    # the two streams; a longer queue makes a batch
+    reqs = [Request(i, mg.TRI, 4, i, 0.0) for i in range(3)]
+    srv = BatchServer(budget_bytes=1 << 30, lanes=2, caps=LaneCaps(max_meshes=8), device="cpu", use_graph=False,
+                      streams=2, depth=1, batch_min=4)
+    st = srv.run(reqs)
+    assert st["failed"] == 0 and FakeBuilder.launches == 3 and FakeBatchBuilder.launches == 0
+    # two streams: the first two start together, the third behind one of them
+    assert abs(reqs[0].t_done - reqs[1].t_done) < GPU_S and reqs[2].t_done > reqs[0].t_done
+    reqs = [Request(i, mg.TRI, 4, i, 0.0) for i in range(12)]
+    st = srv.run(reqs)
+    assert st["failed"] == 0 and FakeBatchBuilder.launches >= 1
 
 
 def test_batch_server_rejects_what_no_lane_holds(fake_cuda):
@@ -155,7 +200,7 @@ def test_batch_server_watchdog_on_a_stream_that_never_completes(fake_cuda):
     srv = BatchServer(budget_bytes=1 << 30, lanes=2, caps=LaneCaps(max_meshes=4), device="cpu", use_graph=False,
                       deadline_s=0.2)
     t = time.perf_counter()
-    with pytest.raises(serve.ServeTimeout, match="batch of"):
+    with pytest.raises(serve.ServeTimeout, match="unit of"):
         srv.run(small_requests(10))
     assert 0.2 <= time.perf_counter() - t < 5.0
 
