@@ -770,6 +770,7 @@ def serving_summary(args):
         loads[str(ld)] = {"rate_req_per_s": ld * sat["req_per_s"],
                           "plain": {k: rp.get(k) for k in keys}, "batched": {k: rb.get(k) for k in keys}}
     policy = {"streams": len(batched.streams), "depth": batched.depth, "batch_min": batched.batch_min,
+              "batch_elems": batched.batch_elems,
               "batch_slots": len(batched.lanes)}
     del plain, batched
 

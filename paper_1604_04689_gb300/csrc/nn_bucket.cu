@@ -81,28 +81,31 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// Ascending bitonic sorting network over a[0..N) held in registers (all
-// indices are compile-time constants once unrolled).
+__host__ __device__ constexpr int pow2_ceil(int n) { return n <= 1 ? 1 : 2 * pow2_ceil((n + 1) / 2); }
+
+// Ascending sort of a[0..N) held in registers by Batcher's odd-even merge
+// sort (Knuth, TAOCP vol. 3, 5.3.4), laid out for the next power of two P
+// >= N and pruned to N: every comparator puts the minimum at its lower index,
+// so the +infinity (EMPTY) entries at N..P-1 never move and a comparator that
+// touches one of them is a no-op.  Every index is a compile-time constant
+// once the loops are unrolled, so the array stays in registers.
 template <int N, int M>
 __device__ __forceinline__ void sort_net(uint32_t (&a)[M]) {
-    static_assert(N <= M && (N & (N - 1)) == 0, "network size");
+    static_assert(N <= M, "network size");
+    constexpr int P = pow2_ceil(N);
 #pragma unroll
-    for (int k = 2; k <= N; k <<= 1) {
+    for (int p = 1; p < P; p <<= 1) {
 #pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int k = p; k >= 1; k >>= 1) {
+            // comparators (lo, lo + k) for lo = j + i, j = k mod p + 2k t, 0 <= i < k,
+            // both ends in one block of 2p
 #pragma unroll
-            for (int i = 0; i < N; ++i) {
-                const int q = i ^ j;
-                if (q > i) {
-                    const uint32_t x = a[i], y = a[q];
-                    const uint32_t lo = min(x, y), hi = max(x, y);
-                    if ((i & k) == 0) {
-                        a[i] = lo;
-                        a[q] = hi;
-                    } else {
-                        a[i] = hi;
-                        a[q] = lo;
-                    }
+            for (int lo = 0; lo < P; ++lo) {
+                const int r = lo - k % p, hi = lo + k;
+                if (r >= 0 && r % (2 * k) < k && hi < N && lo / (2 * p) == hi / (2 * p)) {
+                    const uint32_t x = a[lo], y = a[hi];
+                    a[lo] = min(x, y);
+                    a[hi] = max(x, y);
                 }
             }
         }
@@ -116,10 +119,15 @@ __device__ __forceinline__ void sort_prefix(uint32_t (&a)[M], uint32_t n_warp) {
     if (n_warp <= 1) return;
     if (n_warp <= 2) sort_net<2>(a);
     else if (n_warp <= 4) sort_net<4>(a);
+    else if (n_warp <= 6) sort_net<6>(a);
     else if (n_warp <= 8) sort_net<8>(a);
     else if constexpr (M >= 16) {
-        if (n_warp <= 16 || M == 16) sort_net<16>(a);
-        else sort_net<M>(a);
+        if (n_warp <= 12) sort_net<12>(a);
+        else if (n_warp <= 16 || M == 16) sort_net<16>(a);
+        else if constexpr (M >= 24) {
+            if (n_warp <= 24) sort_net<24>(a);
+            else sort_net<M>(a);
+        }
     }
 }
 

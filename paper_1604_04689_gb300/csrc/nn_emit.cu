@@ -35,6 +35,27 @@ __device__ __forceinline__ bool node_in(const EmitParams& p, int32_t v, uint32_t
 
 __host__ __device__ inline bool ranged(const EmitParams& p) { return p.node_lo != 0 || p.node_span != p.n_nodes; }
 
+// The npe (<= 8) nodes of a mixed mesh's element at conn[a ..]: 16-byte loads
+// when the element starts on a 16-byte boundary (hex and tet elements of a
+// mesh whose earlier elements all have 4 or 8 nodes), else one load per node.
+// Entries from npe on are 0.
+__device__ __forceinline__ void load_mixed_nodes(const int32_t* conn, int64_t a, int npe, int32_t* nd) {
+    const int32_t* src = conn + a;
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0 && (npe == 4 || npe == 8)) {
+        const int4 x = __ldg(reinterpret_cast<const int4*>(src));
+        nd[0] = x.x; nd[1] = x.y; nd[2] = x.z; nd[3] = x.w;
+        if (npe == 8) {
+            const int4 y = __ldg(reinterpret_cast<const int4*>(src) + 1);
+            nd[4] = y.x; nd[5] = y.y; nd[6] = y.z; nd[7] = y.w;
+        } else {
+            nd[4] = nd[5] = nd[6] = nd[7] = 0;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) nd[q] = q < npe ? __ldg(src + q) : 0;
+    }
+}
+
 // Per-incidence callback signature: (v, nf, e, x0, x1, x2) with x_s = -1 for none.
 template <int TYPE, class F>
 __device__ __forceinline__ void visit_elem(const int32_t* nd, int64_t e, int64_t n_nodes, int32_t* status,
@@ -112,8 +133,7 @@ __device__ __forceinline__ void walk_cta(const EmitParams& p, F&& f) {
                 continue;
             }
             int32_t nd[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) nd[q] = q < b - a ? __ldg(p.conn + a + q) : 0;
+            load_mixed_nodes(p.conn, a, (int)(b - a), nd);
             visit_elem<NN_MIXED>(nd, u, p.n_nodes, p.status, t, f);
         }
     }
@@ -198,12 +218,11 @@ __device__ __forceinline__ int load_unit(const EmitParams& p, int64_t u, int32_t
             return NN_HEX;
         }
         const int npe = (int)(b - a);
+        load_mixed_nodes(p.conn, a, npe, nd);
         bool v = true;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            nd[q] = q < npe ? __ldg(p.conn + a + q) : 0;
+        for (int q = 0; q < 8; ++q)
             if (q < npe) v = v && nd[q] >= 0 && (int64_t)nd[q] < p.n_nodes;
-        }
         if (!v) set_status(p.status, NN_ERR_NODE_RANGE);
         ok[0] = v;
         return t;

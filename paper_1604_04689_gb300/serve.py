@@ -10,7 +10,7 @@ the fewest elements in flight.  Whenever a stream is open, the requests that
 have arrived are admitted at once: fewer than ``batch_min`` waiting requests
 leave one by one as single-mesh builds; ``batch_min`` or more leave together
 as one batch on a free slot (in arrival order, while they fit the slot's
-capacity and the device-memory budget).  So a lightly loaded server answers
+capacity, ``batch_elems`` elements and the device-memory budget).  So a lightly loaded server answers
 each request as soon as it arrives, with small requests running beside large
 ones instead of behind them, and a loaded one amortises the launch sequence
 over every request that queued while all streams were busy.  Each request's
@@ -131,14 +131,16 @@ class Admission:
         c = self.caps
         return r.n_elems <= c.max_elems and r.n_nodes <= c.max_nodes and r.n_conn <= c.max_conn
 
-    def form(self, queue: deque, free_bytes: int, limit: Optional[int] = None) -> list:
+    def form(self, queue: deque, free_bytes: int, limit: Optional[int] = None,
+             max_elems: Optional[int] = None) -> list:
         c = self.caps
         cap = c.max_meshes if limit is None else min(limit, c.max_meshes)
+        emax = c.max_elems if max_elems is None else min(max_elems, c.max_elems)
         batch, e, nn_, cc, b = [], 0, 0, 0, 0
         while queue and len(batch) < cap:
             r = queue[0]
-            if (e + r.n_elems > c.max_elems or nn_ + r.n_nodes > c.max_nodes or cc + r.n_conn > c.max_conn
-                    or b + r.device_bytes() > free_bytes):
+            if (e + r.n_elems > (emax if batch else c.max_elems) or nn_ + r.n_nodes > c.max_nodes
+                    or cc + r.n_conn > c.max_conn or b + r.device_bytes() > free_bytes):
                 break
             queue.popleft()
             batch.append(r)
@@ -265,7 +267,8 @@ def _stats(reqs: List[Request], t_first: float, t_last: float) -> dict:
 class BatchServer:
     def __init__(self, budget_bytes: int = 40 << 30, lanes: int = 2, caps: Optional[LaneCaps] = None,
                  want: int = nn.WANT_BOTH, device=None, use_graph: bool = True, keep_results: bool = False,
-                 deadline_s: float = 60.0, streams: int = 2, depth: int = 2, batch_min: int = 8):
+                 deadline_s: float = 60.0, streams: int = 2, depth: int = 2, batch_min: int = 8,
+                 batch_elems: Optional[int] = None):
         import torch
         self.torch = torch
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -275,6 +278,9 @@ class BatchServer:
         self.keep = keep_results
         self.depth = max(1, depth)          # units in flight per stream
         self.batch_min = max(2, batch_min)  # queued requests that make a batch (fewer: the oldest alone)
+        # elements a batch takes: at most the small capacity class, whose graph's
+        # fixed costs are small (this bounds the latency of a batch's members)
+        self.batch_elems = batch_elems if batch_elems is not None else SMALL_CAPS.max_elems
         self.streams = [torch.cuda.Stream(self.device) for _ in range(max(1, streams))]
         self.lanes = [_Lane(torch, self.caps, self.device, want, use_graph, self.streams[i % len(self.streams)])
                       for i in range(lanes)]
@@ -370,7 +376,8 @@ class BatchServer:
                 if lane is None:
                     lane = next((l for l in self.lanes if not l.busy), None)
                 many = len(queue) >= self.batch_min and lane is not None
-                batch = self.admission.form(queue, self.budget - used, limit=None if many else 1)
+                batch = self.admission.form(queue, self.budget - used, limit=None if many else 1,
+                                            max_elems=self.batch_elems)
                 if batch:
                     k0 = len(admitted)
                     admitted.extend(batch)
