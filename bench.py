@@ -96,6 +96,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=10000, help="serve workload: number of requests")
     ap.add_argument("--load", type=float, default=0.8, help="serve workload: arrival rate / plain saturated rate")
     ap.add_argument("--loads", default="", help="serve workload: also sweep these comma-separated loads")
+    ap.add_argument("--table1", action="store_true",
+                    help="time triangle grids at the vertex counts of the paper's Table 1 (synthetic stand-in)")
     ap.add_argument("--chunk-frac", type=float, default=0.0,
                     help="chunked build with this fraction of the whole-mesh workspace (prints its own line)")
     ap.add_argument("--host-io", action="store_true",
@@ -395,6 +397,66 @@ def sortpipe_arm(args):
 
 # ---------------------------------------------------------------- ours
 
+# Table 1's scanned surfaces (vertex and triangle counts as the table prints
+# them, in thousands), the paper's GT640 node / element times (ms), and the
+# side of the random-diagonal triangle grid with about as many vertices
+TABLE1 = (("Armadillo", 172000, 346000, 50.0, 22.1, 415), ("Angel", 237000, 474000, 66.7, 29.4, 487),
+          ("Skeleton Hand", 327000, 655000, 89.1, 38.3, 572), ("Dragon", 437000, 871000, 112.7, 48.5, 661),
+          ("Happy Buddha", 543000, 1088000, 138.5, 60.6, 737),
+          ("Turbine Blade", 882000, 1765000, 221.3, 93.3, 939))
+
+
+def table1_sweep(args):
+    """Synthetic stand-in for Table 1: a triangle grid per scanned surface,
+    with about its vertex count (same ~2 triangles per vertex and mean valence
+    ~6), timed for the node rows, the element rows and both (CUDA events, L2
+    flushed before each build, median of --steps).  The paper's own GT640
+    times are printed beside them for context."""
+    import torch
+    from paper_1604_04689_gb300 import meshgen as mg
+    from paper_1604_04689_gb300 import nn
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20), dtype=torch.uint8, device=dev)
+    b = nn.Builder(dev)
+    rows = []
+    for name, v_paper, t_paper, node_ms, elem_ms, n in TABLE1:
+        mesh = mg.tri_grid(n, 7)
+        dm = nn.DeviceMesh.from_host(mesh, device=dev)
+        row = {"mesh": name, "paper_V": v_paper, "paper_T": t_paper, "paper_gt640_ms": [node_ms, elem_ms],
+               "grid": f"{n}x{n}", "V": mesh.n_nodes, "T": mesh.n_elems}
+        for label, want in (("nodes", nn.WANT_NODES), ("elems", nn.WANT_ELEMS), ("both", nn.WANT_BOTH)):
+            ws_bytes = b.query(dm, want)[0]
+            ws = b.workspace(ws_bytes)
+            out = b.alloc_outputs(dm, want)
+            for _ in range(max(args.warmup, 3)):
+                b.launch(dm, want, out, ws=ws, ws_bytes=ws_bytes)
+            times = []
+            for _ in range(args.steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st = b.launch(dm, want, out, ws=ws, ws_bytes=ws_bytes)
+                e1.record(stream)
+                if st:
+                    raise nn.NNError(st, "launch")
+                torch.cuda.synchronize(dev)
+                times.append(e0.elapsed_time(e1))
+            if int(b.status.item()) != 0:
+                raise RuntimeError("device status " + nn.STATUS[int(b.status.item())])
+            times.sort()
+            ms = times[len(times) // 2]
+            row[f"{label}_ms"] = ms
+            row[f"{label}_mtri_per_s"] = mesh.n_elems / (ms * 1e-3) / 1e6
+            del ws, out
+        rows.append(row)
+    print(json.dumps({"table1_stand_in": rows, "steps": args.steps, "l2": "flushed before every timed build",
+                      "data": "synthetic: random-diagonal triangle grids, seed 7, node ids and element order permuted"}),
+          flush=True)
+
+
 def chunked_bench(args):
     """Chunked build (nodes in consecutive-id chunks, each within a bounded
     workspace) beside the single build of the same mesh, same process, L2
@@ -536,6 +598,9 @@ def main():
         return
     if args.chunk_frac > 0:
         chunked_bench(args)
+        return
+    if args.table1:
+        table1_sweep(args)
         return
 
     import torch
@@ -917,7 +982,8 @@ def launches_per_build(plan, want="both"):
 
 # the sources that compile the single-mesh build's kernels and their launch
 # plan: traffic counters taken on other sources no longer describe them
-MEASURED_SOURCES = ("nn_api.cu", "nn_bucket.cu", "nn_compact.cu", "nn_device.cuh", "nn_emit.cu", "nn_internal.h")
+MEASURED_SOURCES = ("nn_api.cu", "nn_bucket.cu", "nn_bulk.cuh", "nn_compact.cu", "nn_device.cuh", "nn_emit.cu",
+                    "nn_internal.h")
 
 
 def source_digest():

@@ -23,6 +23,7 @@ struct nn_handle {
     int sb_override = -1;      // fixed bucket width (tests / tuning), -1 = automatic
     int part_mode = -1;        // -1 automatic, 0 one scattered store per record (tests)
     int64_t hist_chunk_override = 0;  // > 0: count at most this many buckets per walk (tests)
+    int emit_ctas_override = 0;       // > 0: at most this many element-walk CTAs (tests)
     nn_tuning tuning{};        // nn_set_tuning: bucket width, block size, CTAs per SM (0 = automatic)
     // per-stage timing (nn_profile_*)
     bool prof = false;
@@ -206,6 +207,7 @@ nn_status make_plan_range(const nn_handle* h, const nn_mesh* m, int want, int64_
     p.emit_smem = std::max<size_t>(16, (size_t)p.hist_chunk * 4);
     const int cps = p.emit_smem + 2048 <= 113 * 1024 ? 2 : 1;
     p.G = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sms * cps, (n_units + 2047) / 2048));
+    if (h->emit_ctas_override > 0) p.G = std::min(p.G, h->emit_ctas_override);
     p.G_part = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sms * 2, (n_units + 511) / 512));
     if (f.cshift >= 0)  // tile-sorted passes: 256-thread CTAs, several per SM
         p.G_part = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sms * 4, (n_units + 511) / 512));
@@ -719,6 +721,7 @@ nn_status nn_create(nn_handle** out) {
     if (const char* e = std::getenv("NN_SB")) h->sb_override = std::atoi(e);
     if (const char* e = std::getenv("NN_PART")) h->part_mode = std::strcmp(e, "scatter") == 0 ? 0 : -1;
     if (const char* e = std::getenv("NN_HIST_CHUNK")) h->hist_chunk_override = std::atoll(e);
+    if (const char* e = std::getenv("NN_EMIT_CTAS")) h->emit_ctas_override = std::atoi(e);
     if (const char* e = std::getenv("NN_BUCKET_SMEM_KB")) {
         size_t kb = (size_t)std::atol(e);
         if (kb >= 32 && kb * 1024 <= h->smem_optin - 1024) h->bucket_smem = kb * 1024;

@@ -142,12 +142,40 @@ __device__ __forceinline__ void walk_cta(const EmitParams& p, F&& f) {
 // Counts per bucket of this CTA's element slice, in shared memory.  When the
 // buckets outnumber the shared counters (hist_chunk), the slice is walked once
 // per chunk of buckets.
+//
+// With twice as many buckets as 32-bit counters fit (p.hist_chunk < B <=
+// 2 p.hist_chunk) the slice is first counted in one walk with two 16-bit
+// counters per word.  A count that would pass 65535 carries into its
+// neighbour; the thread whose add would do so sees the old value, flags the
+// CTA, and the CTA counts its slice again with 32-bit counters.
 template <int TYPE, bool RANGED>
 __global__ void __launch_bounds__(EMIT_THREADS) k_hist(EmitParams p) {
-    extern __shared__ uint32_t sh_hist[];
+    extern __shared__ uint32_t sh_hist[];  // (no static shared memory: the dynamic part may take the whole limit)
     const int64_t B = p.n_buckets;
     const int sb = p.fmt.sb;
     uint32_t* row = p.hist + (int64_t)blockIdx.x * B;
+    if (B > p.hist_chunk && B <= 2 * p.hist_chunk) {
+        const int64_t words = (B + 1) / 2;
+        for (int64_t w = threadIdx.x; w < words; w += blockDim.x) sh_hist[w] = 0;
+        __syncthreads();
+        bool wrapped = false;
+        walk_cta<TYPE>(p, [&](int32_t v, int nf, int64_t, int32_t, int32_t, int32_t) {
+            uint32_t vr;
+            if (!node_in<RANGED>(p, v, vr)) return;  // another chunk's node
+            const uint32_t b = vr >> sb, sh = (b & 1u) * 16u;
+            const uint32_t old = atomicAdd(&sh_hist[b >> 1], 1u << sh);
+            wrapped |= ((old >> sh) & 0xFFFFu) == 0xFFFFu;
+            if (nf && p.nfc && NN_IN(b, B, p.status)) atomicAdd(&p.nfc[b], 1u);  // rare: degenerate elements only
+        });
+        if (!__syncthreads_or(wrapped)) {
+            for (int64_t b = threadIdx.x; b < B; b += blockDim.x)
+                if (NN_IN((int64_t)blockIdx.x * B + b, p.hist_words, p.status))
+                    row[b] = (sh_hist[b >> 1] >> ((b & 1) * 16)) & 0xFFFFu;
+            return;
+        }
+        __syncthreads();  // a count wrapped: count again below (the repeated-node counts are complete)
+    }
+    const bool nf_done = B > p.hist_chunk && B <= 2 * p.hist_chunk;
     for (int64_t c0 = 0; c0 < B; c0 += p.hist_chunk) {
         const int64_t nc = min(B - c0, p.hist_chunk);
         for (int64_t b = threadIdx.x; b < nc; b += blockDim.x) sh_hist[b] = 0;
@@ -157,7 +185,7 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_hist(EmitParams p) {
             if (!node_in<RANGED>(p, v, vr)) return;  // another chunk's node
             const int64_t b = (int64_t)(vr >> sb) - c0;
             if (b >= 0 && b < nc) atomicAdd(&sh_hist[b], 1u);
-            if (nf && c0 == 0 && p.nfc && NN_IN(vr >> sb, B, p.status))
+            if (nf && c0 == 0 && !nf_done && p.nfc && NN_IN(vr >> sb, B, p.status))
                 atomicAdd(&p.nfc[vr >> sb], 1u);  // rare: degenerate elements only
         });
         __syncthreads();
@@ -375,16 +403,21 @@ template <int TYPE>
 __host__ __device__ constexpr size_t coarse_smem() {
     return (size_t)SortShape<TYPE>::TILE * 17 + 3 * 256 * 4;
 }
-constexpr int FINE_RPT = 4;
-constexpr int FINE_TILE = SORT_THREADS * FINE_RPT;
+// Records per thread of a fine-pass tile: 4, or 8 when a coarse region has
+// at least 512 buckets (then a 1024-record tile has about two records per
+// bucket, and its one cursor atomic per bucket present would come close to
+// one per two records; with 256 buckets the larger tile measured slower).
+constexpr int FINE_RPT_WIDE_DIGITS = 512;
+__host__ __device__ constexpr int fine_rpt(int nd) { return nd >= FINE_RPT_WIDE_DIGITS ? 8 : 4; }
 constexpr int FINE_DIGITS = 4096;  // buckets per coarse region: at most 256 x 4096 buckets in all
 // shared memory of the fine pass for nd digits per coarse region and rb-byte
 // records: two tile stages (bulk-copy targets, 16 bytes of slack for an odd
 // 8-byte first record), the tile in digit order with its digits, three
 // per-digit tables and the first work item of every coarse region
-__host__ __device__ constexpr size_t fine_stage_bytes(int rb) { return (size_t)FINE_TILE * rb + 16; }
+__host__ __device__ constexpr size_t fine_stage_bytes(int tile, int rb) { return (size_t)tile * rb + 16; }
 __host__ __device__ constexpr size_t fine_smem(int nd, int rb) {
-    return 2 * fine_stage_bytes(rb) + (size_t)FINE_TILE * 18 + 3 * (size_t)nd * 4 + 257 * 4;
+    return 2 * fine_stage_bytes(SORT_THREADS * fine_rpt(nd), rb) + (size_t)SORT_THREADS * fine_rpt(nd) * 18 +
+           3 * (size_t)nd * 4 + 257 * 4;
 }
 constexpr size_t FINE_SMEM = fine_smem(FINE_DIGITS, 16);
 
@@ -509,10 +542,11 @@ __global__ void __launch_bounds__(SORT_THREADS) k_part_coarse(EmitParams p) {
 // memory by a bulk asynchronous copy issued while the CTA still sorts and
 // writes the tile before it (two stages, one mbarrier each, bounded waits),
 // so the tile loads overlap the in-tile sort instead of stalling it.
-template <int RB>
+template <int RB, int FINE_RPT>
 __global__ void __launch_bounds__(SORT_THREADS) k_part_fine(EmitParams p, const uint32_t* bstart) {
+    constexpr int FINE_TILE = SORT_THREADS * FINE_RPT;
     extern __shared__ __align__(16) uint8_t sm[];
-    constexpr uint32_t SB = (uint32_t)fine_stage_bytes(RB);
+    constexpr uint32_t SB = (uint32_t)fine_stage_bytes(FINE_TILE, RB);
     uint8_t* const stage = sm;  // [2][SB]
     ulonglong2* out = reinterpret_cast<ulonglong2*>(sm + 2 * SB);
     uint16_t* odig = reinterpret_cast<uint16_t*>(out + FINE_TILE);
@@ -601,7 +635,15 @@ __global__ void __launch_bounds__(SORT_THREADS) k_part_fine(EmitParams p, const 
         const int64_t fb0 = (int64_t)d << cs;
         const uint32_t n = sh_tile[st][2] - sh_tile[st][1];
         const uint8_t* const src = stage + st * SB + sh_tile[st][3];
-        ulonglong2 x[FINE_RPT];
+        // a thread keeps its records' digits and ranks, and the records
+        // themselves in registers when it holds four (else they are read
+        // from the stage again when placed)
+        auto rec_at = [&](uint32_t r) {
+            if constexpr (RB == 8) return make_ulonglong2(reinterpret_cast<const unsigned long long*>(src)[r], 0);
+            else return reinterpret_cast<const ulonglong2*>(src)[r];
+        };
+        constexpr int XR = FINE_RPT <= 4 ? FINE_RPT : 1;
+        ulonglong2 x[XR];
         uint16_t rk[FINE_RPT];
         uint16_t dg[FINE_RPT];
 #pragma unroll
@@ -610,9 +652,9 @@ __global__ void __launch_bounds__(SORT_THREADS) k_part_fine(EmitParams p, const 
             rk[k] = 0xFFFF;
             dg[k] = 0;
             if (r < n) {
-                if constexpr (RB == 8) x[k] = make_ulonglong2(reinterpret_cast<const unsigned long long*>(src)[r], 0);
-                else x[k] = reinterpret_cast<const ulonglong2*>(src)[r];
-                const Rec rr{x[k].x, x[k].y};
+                const ulonglong2 xr = rec_at(r);
+                if constexpr (FINE_RPT <= 4) x[k] = xr;
+                const Rec rr{xr.x, xr.y};
                 dg[k] = (uint16_t)rec_get(rr, f.off_fb, cs);
             }
         }
@@ -627,7 +669,8 @@ __global__ void __launch_bounds__(SORT_THREADS) k_part_fine(EmitParams p, const 
         for (int k = 0; k < FINE_RPT; ++k) {
             if (rk[k] == 0xFFFF) continue;
             const uint32_t q = dof[dg[k]] + rk[k];
-            out[q] = x[k];
+            if constexpr (FINE_RPT <= 4) out[q] = x[k];
+            else out[q] = rec_at(threadIdx.x + k * SORT_THREADS);
             odig[q] = dg[k];
         }
         __syncthreads();
@@ -775,19 +818,21 @@ cudaError_t launch_part_coarse(const EmitParams& p, cudaStream_t s) {
 
 // One CTA per resident slot (the SMs times the CTAs its shared memory
 // allows per SM): each CTA works through its tiles with the copies in flight.
-template <int RB>
+template <int RB, int RPT>
 cudaError_t fine_t(const EmitParams& p, const uint32_t* bstart, int sms, cudaStream_t s) {
     const size_t fs = fine_smem(1 << p.fmt.cshift, RB);
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_part_fine<RB>, SORT_THREADS, fs);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_part_fine<RB, RPT>, SORT_THREADS, fs);
     if (e != cudaSuccess) return e;
-    k_part_fine<RB><<<std::max(1, sms * std::max(occ, 1)), SORT_THREADS, fs, s>>>(p, bstart);
+    k_part_fine<RB, RPT><<<std::max(1, sms * std::max(occ, 1)), SORT_THREADS, fs, s>>>(p, bstart);
     return cudaGetLastError();
 }
 
 cudaError_t launch_part_fine(const EmitParams& p, const uint32_t* bstart, int sms, cudaStream_t s) {
     if (p.fmt.cshift <= 0) return cudaSuccess;
-    return p.fmt.rb == 8 ? fine_t<8>(p, bstart, sms, s) : fine_t<16>(p, bstart, sms, s);
+    const bool wide = fine_rpt(1 << p.fmt.cshift) == 8;
+    if (p.fmt.rb == 8) return wide ? fine_t<8, 8>(p, bstart, sms, s) : fine_t<8, 4>(p, bstart, sms, s);
+    return wide ? fine_t<16, 8>(p, bstart, sms, s) : fine_t<16, 4>(p, bstart, sms, s);
 }
 
 cudaError_t launch_part_sorted(const EmitParams& p, const uint32_t* bstart, int sms, cudaStream_t s) {
@@ -827,9 +872,13 @@ cudaError_t set_emit_smem_all(size_t bytes) {
     if (e == cudaSuccess) e = set_sorted_smem<NN_HEX>();
     if (e == cudaSuccess) e = set_sorted_smem<NN_MIXED>();
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_part_fine<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FINE_SMEM);
+        e = cudaFuncSetAttribute(k_part_fine<8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FINE_SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_part_fine<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FINE_SMEM);
+        e = cudaFuncSetAttribute(k_part_fine<8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FINE_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_part_fine<16, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FINE_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_part_fine<16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FINE_SMEM);
     if (e == cudaSuccess) e = set_emit_smem<NN_TRI>(bytes);
     if (e == cudaSuccess) e = set_emit_smem<NN_QUAD>(bytes);
     if (e == cudaSuccess) e = set_emit_smem<NN_TET>(bytes);

@@ -103,12 +103,24 @@ def test_parity_two_level_partition_many_buckets(sb):
     check_against_oracle(m, nn.WANT_BOTH, b, ws_extra=64 * m.n_conn)
 
 
-@pytest.mark.parametrize("chunk", [1, 37, 100])
+@pytest.mark.parametrize("chunk", [1, 37, 100, 600])
 def test_parity_histogram_in_chunks(chunk):
-    """More buckets than shared counters: the histogram walks the elements once per chunk."""
+    """More buckets than shared counters: the histogram walks the elements once per chunk
+    (chunk 600: at most twice as many buckets as counters, one walk with 16-bit counters)."""
     with env(NN_HIST_CHUNK=chunk, NN_SB=6):
         b = nn.Builder()
     check_against_oracle(MESHES["mixed41"](), nn.WANT_BOTH, b, ws_extra=64 * MESHES["mixed41"]().n_conn)
+
+
+def test_histogram_16_bit_count_wraps_and_is_counted_again():
+    """One element-walk CTA over a fan of 300k triangles with 16-bit histogram
+    counters: the hub's bucket passes 65535 records, the CTA sees the wrap
+    and counts its slice again with 32-bit counters."""
+    f = fan(300000)
+    n_buckets = -(-f.n_nodes // 64)
+    with env(NN_HIST_CHUNK=n_buckets // 2 + 1, NN_SB=6, NN_EMIT_CTAS=1):
+        b = nn.Builder()
+    check_against_oracle(f, nn.WANT_BOTH, b)
 
 
 def fan(n_tri, hub=0, extra_nodes=3):
