@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_part_b(BatchTables bt, uint32
 #pragma unroll
                 for (int s = 0; s < 3; ++s) {
                     if (s >= K) break;
-                    const int32_t y = nd[nbr_of(t, i, s)];
+                    const int32_t y = nbr_node(t, nd, i, s);
                     rec_put(r, y == v ? 0ull : (uint64_t)(uint32_t)(y + 1), f.off_n + s * f.nb);
                 }
             }

@@ -221,5 +221,18 @@ __device__ __forceinline__ int nbr_of(int t, int i, int s) {
     }
 }
 __device__ __forceinline__ int k_of(int t) { return (t == NN_TRI || t == NN_QUAD) ? 2 : 3; }
+// The node at the far end of local edge s at local node i of an element of
+// run-time type t, read from the element's nodes nd[0..8).  Called with i and
+// s fixed by unrolled loops, every index below is a compile-time constant, so
+// nd stays in registers (an index computed at run time, as nbr_of gives,
+// would put the array in local memory).  Every index is below 8.
+__device__ __forceinline__ int32_t nbr_node(int t, const int32_t* nd, int i, int s) {
+    switch (t) {
+        case NN_TRI: return nd[ElemT<NN_TRI>::nbr(i, s)];
+        case NN_QUAD: return nd[ElemT<NN_QUAD>::nbr(i, s)];
+        case NN_TET: return nd[ElemT<NN_TET>::nbr(i, s)];
+        default: return nd[ElemT<NN_HEX>::nbr(i, s)];
+    }
+}
 
 }  // namespace nn

@@ -84,8 +84,7 @@ __device__ __forceinline__ void visit_elem(const int32_t* nd, int64_t e, int64_t
         for (int s = 0; s < 3; ++s) {
             int32_t y = -1;
             if (s < K) {
-                int li = TYPE == NN_MIXED ? nbr_of(t, i, s) : ElemT<(TYPE == NN_MIXED ? NN_HEX : TYPE)>::nbr(i, s);
-                y = nd[li];
+                y = TYPE == NN_MIXED ? nbr_node(t, nd, i, s) : nd[ElemT<(TYPE == NN_MIXED ? NN_HEX : TYPE)>::nbr(i, s)];
                 if (y == v) y = -1;
             }
             x[s] = y;
@@ -338,9 +337,9 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_part(EmitParams p) {
 #pragma unroll
                     for (int s = 0; s < 3; ++s) {
                         if (s >= K) break;
-                        const int li = TYPE == NN_MIXED ? nbr_of(tk, i, s)
-                                                        : ElemT<(TYPE == NN_MIXED ? NN_HEX : TYPE)>::nbr(i, s);
-                        const int32_t y = e_nd[li];
+                        const int32_t y = TYPE == NN_MIXED
+                                              ? nbr_node(tk, e_nd, i, s)
+                                              : e_nd[ElemT<(TYPE == NN_MIXED ? NN_HEX : TYPE)>::nbr(i, s)];
                         rec_put(r, y == v ? 0ull : (uint64_t)(uint32_t)(y + 1), f.off_n + s * f.nb);
                     }
                 }
@@ -439,8 +438,8 @@ __device__ __forceinline__ Rec make_rec(const RecFmt& f, const int32_t* e_nd, in
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
             if (s >= K) break;
-            const int li = TYPE == NN_MIXED ? nbr_of(t, i, s) : ElemT<(TYPE == NN_MIXED ? NN_HEX : TYPE)>::nbr(i, s);
-            const int32_t y = e_nd[li];
+            const int32_t y = TYPE == NN_MIXED ? nbr_node(t, e_nd, i, s)
+                                               : e_nd[ElemT<(TYPE == NN_MIXED ? NN_HEX : TYPE)>::nbr(i, s)];
             rec_put(r, y == v ? 0ull : (uint64_t)(uint32_t)(y + 1), f.off_n + s * f.nb);
         }
     }
