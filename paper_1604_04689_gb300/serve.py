@@ -9,7 +9,9 @@ most ``depth`` units in flight, and a new unit goes to the open stream with
 the fewest elements in flight.  Whenever a stream is open, the requests that
 have arrived are admitted at once: fewer than ``batch_min`` waiting requests
 leave one by one as single-mesh builds; ``batch_min`` or more leave together
-as one batch on a free slot (in arrival order, while they fit the slot's
+as one batch on a free slot, and once such a backlog has formed every queue
+of two or more leaves as a batch until the queue has emptied (so a loaded
+server does not fall back to single builds while a backlog remains) (in arrival order, while they fit the slot's
 capacity, ``batch_elems`` elements and the device-memory budget).  So a lightly loaded server answers
 each request as soon as it arrives, with small requests running beside large
 ones instead of behind them, and a loaded one amortises the launch sequence
@@ -332,6 +334,7 @@ class BatchServer:
             raise ValueError("budget smaller than the lane workspaces")
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         queue, inflight = deque(), []
+        draining = False                 # a backlog formed: batch every queue of two or more until it empties
         load = [0] * len(self.streams)   # units in flight per stream
         work = [0] * len(self.streams)   # their elements: a unit goes to the least loaded stream
         # statuses: each unit writes those of its requests at their admission
@@ -375,7 +378,9 @@ class BatchServer:
                 lane = next((l for l in self.lanes if not l.busy and l.stream is s), None)
                 if lane is None:
                     lane = next((l for l in self.lanes if not l.busy), None)
-                many = len(queue) >= self.batch_min and lane is not None
+                if len(queue) >= self.batch_min:
+                    draining = True
+                many = (len(queue) >= self.batch_min or (draining and len(queue) >= 2)) and lane is not None
                 batch = self.admission.form(queue, self.budget - used, limit=None if many else 1,
                                             max_elems=self.batch_elems)
                 if batch:
@@ -419,7 +424,11 @@ class BatchServer:
                     inflight.append(dict(reqs=batch, bufs=bufs, start=ev_start, done=ev_done, lane=lane, si=si,
                                          t_launch=time.perf_counter()))
                     self.batches += 1
+                    if not queue:
+                        draining = False
                     continue
+            if not queue:
+                draining = False
             if not inflight and not queue and pending:
                 time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 0.001)))
             elif inflight:
