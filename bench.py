@@ -914,6 +914,7 @@ def end_to_end(torch, nn, b, mesh, dm, want, ws, ws_bytes, out, steps, dev, worl
     start(0)
     finish(0)
     torch.cuda.synchronize(dev)
+    link = host_link(torch, dev, slots[0], h_conn, sU, sD)
     counts["h2d"] = counts["d2h"] = 0
     t0 = time.perf_counter()
     for i in range(steps):
@@ -925,9 +926,51 @@ def end_to_end(torch, nn, b, mesh, dm, want, ws, ws_bytes, out, steps, dev, worl
     dt = time.perf_counter() - t0
     if int(b.status.item()) != 0:
         raise RuntimeError("device status after end-to-end leg: " + nn.STATUS[int(b.status.item())])
+    ms = dt * 1e3 / steps
+    link["frac"] = link["bound_ms_per_step"] / ms  # the step's share of its host-link bound
     return {"value": world * mesh.n_elems * steps / dt / 1e6, "unit": "Melem/s",
             "h2d_bytes_per_step": counts["h2d"] // steps, "d2h_bytes_per_step": counts["d2h"] // steps,
-            "ms_per_step": dt * 1e3 / steps, "pipelined": "uploads, builds, row-pointer and column downloads on four streams"}
+            "ms_per_step": ms, "pipelined": "uploads, builds, row-pointer and column downloads on four streams",
+            "host_link": link}
+
+
+def host_link(torch, dev, sl, h_conn, s_up, s_down):
+    """The host link's own rate on one step's transfers: the connectivity
+    upload alone, then the downloads of both CSRs alone (row pointers and the
+    used part of col, as a step makes them), pinned memory, CUDA events on the
+    copy stream, best of three.  A pipelined step cannot beat the slower of
+    the two directions, so that time is the step's host-link bound."""
+    def timed(stream, fn):
+        best = float("inf")
+        for _ in range(3):
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            with torch.cuda.stream(stream):
+                nbytes = fn()
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best, nbytes
+
+    def up():
+        sl["d_conn"].copy_(h_conn, non_blocking=True)
+        return h_conn.numel() * 4
+
+    def down():
+        nbytes = 0
+        for c, (rp, col) in sl["out"].items():
+            n = int(sl["h_rp"][c][-1])
+            sl["h_rp"][c].copy_(rp, non_blocking=True)
+            sl["h_col"][c][:n].copy_(col[:n], non_blocking=True)
+            nbytes += 8 * rp.numel() + 4 * n
+        return nbytes
+
+    up_ms, up_b = timed(s_up, up)
+    down_ms, down_b = timed(s_down, down)
+    return {"h2d_gbs": up_b / (up_ms * 1e-3) / 1e9, "d2h_gbs": down_b / (down_ms * 1e-3) / 1e9,
+            "bound_ms_per_step": max(up_ms, down_ms),
+            "note": "each direction timed alone on this step's transfers; the step's bound is the slower one"}
 
 
 def time_adjacency(torch, nn, b, dm, out, flush, stream, steps):
