@@ -89,3 +89,14 @@ def test_oracle_samples_match_the_workload_kind():
     assert mesh.etype == 3 and "hex grid 101^3" in desc and abs(ratio - 100 ** 3 / 256 ** 3) < 1e-12
     mesh, desc, ratio = bench.oracle_sample("tri2048")
     assert mesh.etype == 0 and abs(ratio - mesh.n_elems / 8_380_418) < 1e-12
+
+
+def test_throughput_at_a_stated_p99_is_the_highest_load_within_it():
+    loads = {"0.5": {"plain": {"req_per_s": 2700.0, "p99_ms": 2.6}, "batched": {"req_per_s": 2701.0, "p99_ms": 2.4}},
+             "0.8": {"plain": {"req_per_s": 4300.0, "p99_ms": 4.6}, "batched": {"req_per_s": 4310.0, "p99_ms": 4.6}},
+             "1.0": {"plain": {"req_per_s": 5280.0, "p99_ms": 11.4}, "batched": {"req_per_s": 5365.0, "p99_ms": 7.2}},
+             "1.5": {"plain": {"req_per_s": 5560.0, "p99_ms": 113.0}, "batched": {"req_per_s": 5960.0, "p99_ms": 90.5}}}
+    assert bench.sustained_at_p99(loads, "plain", 10.0) == 4300.0
+    assert bench.sustained_at_p99(loads, "batched", 10.0) == 5365.0
+    assert bench.sustained_at_p99(loads, "batched", 100.0) == 5960.0   # a later load within the bound counts
+    assert bench.sustained_at_p99(loads, "plain", 1.0) is None
