@@ -859,13 +859,16 @@ def serving_summary(args):
             "loads": loads}
 
 
+E2E_SLOTS = 2  # buffer sets of the end-to-end pipeline: a build waits for the downloads two steps back
+
+
 def end_to_end(torch, nn, b, mesh, dm, want, ws, ws_bytes, out, steps, dev, world):
     """Same metric through the C ABI with host buffers.  Every step copies its
     connectivity host -> device from pinned memory, builds, and copies both
     CSRs device -> host into pinned memory (row pointers, then the used part of
     col).  Steps are pipelined the way a host-fed service runs them: uploads on
     one stream, builds on another, row-pointer downloads on a third and column
-    downloads on a fourth, two buffer sets, and the column downloads of step i
+    downloads on a fourth, E2E_SLOTS buffer sets, and the column downloads of step i
     enqueued once its row pointers (and so its sizes) have arrived, while step
     i + 1 uploads and builds.  (Row pointers and columns take separate streams:
     in one stream the row pointers of step i + 1, which wait for its build,
@@ -875,7 +878,7 @@ def end_to_end(torch, nn, b, mesh, dm, want, ws, ws_bytes, out, steps, dev, worl
     sR = torch.cuda.Stream(dev)                    # row-pointer downloads
     h_conn = torch.from_numpy(mesh.conn).pin_memory()
     slots = []
-    for k in range(2):
+    for k in range(E2E_SLOTS):
         d_conn = torch.empty_like(dm.conn)
         o = out if k == 0 else b.alloc_outputs(dm, want)
         slots.append(dict(
@@ -887,19 +890,19 @@ def end_to_end(torch, nn, b, mesh, dm, want, ws, ws_bytes, out, steps, dev, worl
     counts = {"h2d": 0, "d2h": 0}
 
     def start(i):                                  # upload, build and row-pointer download of step i
-        sl = slots[i % 2]
-        sU.wait_event(sl["built"])                 # the build two steps back has read this connectivity
+        sl = slots[i % E2E_SLOTS]
+        sU.wait_event(sl["built"])                 # the build E2E_SLOTS steps back has read this connectivity
         with torch.cuda.stream(sU):
             sl["d_conn"].copy_(h_conn, non_blocking=True)
         sl["up"].record(sU)
         sA.wait_event(sl["up"])
-        sA.wait_event(sl["done"])                  # the downloads two steps back have read these outputs
+        sA.wait_event(sl["done"])                  # the downloads E2E_SLOTS steps back have read these outputs
         st = b.launch(sl["dm"], want, sl["out"], ws=ws, ws_bytes=ws_bytes, stream=sA)
         if st:
             raise nn.NNError(st, "launch")
         sl["built"].record(sA)
         sR.wait_event(sl["built"])
-        sR.wait_event(sl["done"])                  # the host row pointers two steps back have been read
+        sR.wait_event(sl["done"])                  # the host row pointers E2E_SLOTS steps back have been read
         with torch.cuda.stream(sR):
             for c, (rp, _) in sl["out"].items():
                 sl["h_rp"][c].copy_(rp, non_blocking=True)
@@ -907,7 +910,7 @@ def end_to_end(torch, nn, b, mesh, dm, want, ws, ws_bytes, out, steps, dev, worl
         counts["h2d"] += h_conn.numel() * 4
 
     def finish(i):                                 # column downloads of step i, sized by its row pointers
-        sl = slots[i % 2]
+        sl = slots[i % E2E_SLOTS]
         sl["rp"].synchronize()
         sD.wait_event(sl["rp"])
         with torch.cuda.stream(sD):
@@ -936,7 +939,7 @@ def end_to_end(torch, nn, b, mesh, dm, want, ws, ws_bytes, out, steps, dev, worl
     link["frac"] = link["bound_ms_per_step"] / ms  # the step's share of its host-link bound
     return {"value": world * mesh.n_elems * steps / dt / 1e6, "unit": "Melem/s",
             "h2d_bytes_per_step": counts["h2d"] // steps, "d2h_bytes_per_step": counts["d2h"] // steps,
-            "ms_per_step": ms, "pipelined": "uploads, builds, row-pointer and column downloads on four streams",
+            "ms_per_step": ms, "pipelined": f"uploads, builds, row-pointer and column downloads on four streams, {E2E_SLOTS} buffer sets",
             "host_link": link}
 
 
