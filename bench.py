@@ -5,8 +5,8 @@ One step = one full build of BOTH results (neighbor-node CSR and
 neighbor-element CSR) for one seeded synthetic mesh, through the C ABI, with
 the connectivity already resident in HBM.  Metric: Melem/s (mesh elements
 processed per second, whole job).  Default workload: the hex grid 257^3
-(16,974,593 nodes, 16,777,216 hexes, node ids permuted), the largest
-single-GPU configuration; the triangle grid 2048^2, the Kuhn tet grid 161^3
+(16,974,593 nodes, 16,777,216 hexes, node ids permuted), the largest of the
+benchmark's meshes; the triangle grid 2048^2, the Kuhn tet grid 161^3
 and the mixed hex/tet variant of the hex grid are timed in the same run under
 "per_config", and a bounded serving run (batched vs one build per mesh)
 under "serving".
