@@ -170,6 +170,21 @@ def test_batch_server_small_queues_go_alone_on_the_least_loaded_stream(fake_cuda
     assert st["failed"] == 0 and FakeBatchBuilder.launches >= 1
 
 
+def test_batch_server_keeps_batching_a_backlog_until_it_empties(fake_cuda):
+    # one stream of depth one, batches from eight waiting requests: a burst of
+    # nine leaves as a batch of eight (max_meshes) with one request left; the
+    # three that arrive while the batch runs make a queue of four -- fewer
+    # than eight, but the backlog has not emptied, so the four leave as one
+    # batch instead of four single builds
+    reqs = [Request(i, mg.TRI, 4, i, 0.0) for i in range(9)]
+    reqs += [Request(9 + i, mg.TRI, 4, 9 + i, 0.2 * GPU_S) for i in range(3)]
+    srv = BatchServer(budget_bytes=1 << 30, lanes=2, caps=LaneCaps(max_meshes=8), device="cpu", use_graph=False,
+                      streams=1, depth=1, batch_min=8)
+    st = srv.run(reqs)
+    assert st["failed"] == 0 and st["requests"] == 12
+    assert FakeBuilder.launches == 0 and FakeBatchBuilder.launches == 2 and st["batches"] == 2
+
+
 def test_batch_server_rejects_what_no_lane_holds(fake_cuda):
     reqs = small_requests(6)
     reqs.append(Request(6, mg.TRI, 200, 1, 0.001))            # 79,202 triangles: more than a lane's capacity
